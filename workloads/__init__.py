@@ -1,0 +1,298 @@
+"""Seeded synthetic inputs shared by the CUDA path's tests/bench and the oracle.
+
+This module only *generates inputs*: hexahedral box meshes (node coordinates at
+Gauss-Lobatto geometry points plus face connectivity with orientation codes) and
+nodal initial states sampled from closed-form fields.  It contains none of the
+DGSEM arithmetic (no differentiation matrices, metrics, fluxes or time
+integration); the two implementations that consume these inputs each do that
+themselves.
+
+Conventions (they define the mesh interface, Sec. 3.1 and Sec. 5.1 of the paper):
+
+* Element-local volume indices (i, j, k) run along (xi1, xi2, xi3); arrays are
+  stored ``[..., k, j, i]`` with i fastest.
+* Local sides: 0: xi1=-1, 1: xi1=+1, 2: xi2=-1, 3: xi2=+1, 4: xi3=-1, 5: xi3=+1.
+* Side-local face coordinates (p, q): the two remaining volume indices in
+  increasing direction order, i.e. (j,k) on xi1 faces, (i,k) on xi2 faces and
+  (i,j) on xi3 faces.  Face arrays are stored ``[..., q, p]``.
+* Orientation code o in 0..7 maps a face node (p, q) of one element to the node
+  (p', q') of the neighbour's side-local system: (a, b) = (q, p) if o & 1 else
+  (p, q); p' = N - a if o & 2 else a; q' = N - b if o & 4 else b.
+* conn[e, s] = (neighbour element, neighbour local side, o) or (-1 - bc_id, -1, 0)
+  on a boundary.
+"""
+from __future__ import annotations
+
+import itertools
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+# ----------------------------------------------------------------------------
+# node sets used only to *sample* geometry and initial states (numpy library)
+# ----------------------------------------------------------------------------
+
+
+def lobatto_points(N: int) -> np.ndarray:
+    """Gauss-Lobatto points on [-1, 1] (numpy root finder on P'_N)."""
+    if N == 0:
+        return np.array([0.0])
+    from numpy.polynomial import legendre as L
+
+    c = np.zeros(N + 1)
+    c[N] = 1.0
+    inner = np.sort(np.real(L.legroots(L.legder(c)))) if N > 1 else np.array([])
+    return np.concatenate([[-1.0], inner, [1.0]])
+
+
+def gauss_points(N: int) -> np.ndarray:
+    from numpy.polynomial import legendre as L
+
+    return L.leggauss(N + 1)[0]
+
+
+def solution_points(N: int, node_type: int) -> np.ndarray:
+    """node_type 0: Legendre-Gauss, 1: Legendre-Gauss-Lobatto."""
+    return gauss_points(N) if node_type == 0 else lobatto_points(N)
+
+
+# ----------------------------------------------------------------------------
+# element frames: the 24 proper rotations of the cube (signed permutations)
+# ----------------------------------------------------------------------------
+
+
+def cube_rotations() -> list[np.ndarray]:
+    rots = []
+    for perm in itertools.permutations(range(3)):
+        for signs in itertools.product((1, -1), repeat=3):
+            R = np.zeros((3, 3), dtype=np.int64)
+            for r in range(3):
+                R[r, perm[r]] = signs[r]
+            if round(np.linalg.det(R)) == 1:
+                rots.append(R)
+    return rots
+
+
+def orientation_code(pmap) -> int:
+    """Return o such that the map (p, q) -> (p', q') on an N=1 face matches pmap."""
+    for o in range(8):
+        ok = True
+        for p, q in ((0, 0), (1, 0), (0, 1), (1, 1)):
+            a, b = (q, p) if o & 1 else (p, q)
+            pp = 1 - a if o & 2 else a
+            qq = 1 - b if o & 4 else b
+            if (pp, qq) != pmap[(p, q)]:
+                ok = False
+                break
+        if ok:
+            return o
+    raise ValueError("face maps are not a dihedral transform")
+
+
+def _face_corner_xi(s: int, p: int, q: int) -> np.ndarray:
+    """Local reference coordinate (+-1 components) of face corner (p, q) of side s."""
+    l, sgn = s // 2, (-1 if s % 2 == 0 else 1)
+    other = [d for d in range(3) if d != l]
+    xi = np.zeros(3)
+    xi[l] = sgn
+    xi[other[0]] = -1 + 2 * p
+    xi[other[1]] = -1 + 2 * q
+    return xi
+
+
+@dataclass
+class BoxMesh:
+    """A structured box of hexahedra presented as an unstructured mesh."""
+
+    nelem: tuple  # (nx, ny, nz)
+    Ngeo: int
+    coords: np.ndarray  # [K, Ngeo+1, Ngeo+1, Ngeo+1, 3] at LGL points, [e, k, j, i, xyz]
+    conn: np.ndarray  # [K, 6, 3] int32
+    lattice: np.ndarray  # [K, 3] integer lattice position of each element
+    frames: np.ndarray  # [K, 3, 3] local->global signed permutation R (eta = R xi)
+    lo: np.ndarray
+    hi: np.ndarray
+    mapping: str
+
+    @property
+    def K(self) -> int:
+        return self.lattice.shape[0]
+
+    def map_points(self, xi_local: np.ndarray) -> np.ndarray:
+        """Physical coordinates of element-local reference points.
+
+        xi_local: [..., 3] in [-1,1]^3 (same for every element).  Returns
+        [K, ..., 3] using the exact (analytic) mapping, not an interpolant.
+        """
+        h = (self.hi - self.lo) / np.array(self.nelem)
+        eta = np.einsum("kab,...b->k...a", self.frames.astype(float), xi_local)
+        shp = (self.K,) + (1,) * (xi_local.ndim - 1) + (3,)
+        lat = self.lattice.reshape(shp).astype(float)
+        x = self.lo + (lat + (eta + 1.0) / 2.0) * h
+        return _apply_mapping(x, self.mapping, self.lo, self.hi)
+
+    def node_coords(self, N: int, node_type: int) -> np.ndarray:
+        """Exact physical coordinates at the solution nodes, [K, 3, n, n, n]."""
+        r = solution_points(N, node_type)
+        kk, jj, ii = np.meshgrid(r, r, r, indexing="ij")
+        xi = np.stack([ii, jj, kk], axis=-1)  # [k, j, i, 3]
+        x = self.map_points(xi)  # [K, k, j, i, 3]
+        return np.ascontiguousarray(np.moveaxis(x, -1, 1))
+
+
+def _apply_mapping(x: np.ndarray, mapping: str, lo, hi) -> np.ndarray:
+    if mapping == "cartesian":
+        return x
+    if mapping == "sine":
+        # x_i = xi_i + 0.1 * prod_j sin(pi xi_j), xi the global coordinate in [-1,1]^3
+        xi = 2.0 * (x - lo) / (hi - lo) - 1.0
+        bump = 0.1 * np.prod(np.sin(np.pi * xi), axis=-1, keepdims=True)
+        return lo + (xi + bump + 1.0) * (hi - lo) / 2.0
+    raise ValueError(mapping)
+
+
+def box_mesh(nelem=(4, 4, 4), lo=(0.0, 0.0, 0.0), hi=(2 * math.pi,) * 3, Ngeo: int = 1,
+             periodic=(True, True, True), mapping: str = "cartesian", reorient_seed=None,
+             bc_ids=None) -> BoxMesh:
+    """Box of nx*ny*nz hexahedra.
+
+    reorient_seed: if not None, every element gets a random proper rotation of its
+    local frame (exercises side orientations).  bc_ids: 6 boundary ids for the
+    box faces (-x,+x,-y,+y,-z,+z); default 0 everywhere.
+    """
+    nx, ny, nz = nelem
+    lo = np.asarray(lo, float)
+    hi = np.asarray(hi, float)
+    bc_ids = bc_ids if bc_ids is not None else [0] * 6
+    lattice = np.array([(a, b, c) for c in range(nz) for b in range(ny) for a in range(nx)], dtype=np.int64)
+    K = len(lattice)
+    rots = cube_rotations()
+    if reorient_seed is None:
+        frames = np.tile(np.eye(3, dtype=np.int64), (K, 1, 1))
+    else:
+        rng = np.random.default_rng(reorient_seed)
+        frames = np.stack([rots[rng.integers(len(rots))] for _ in range(K)])
+    index = {tuple(p): e for e, p in enumerate(lattice)}
+    dims = np.array(nelem)
+    conn = np.zeros((K, 6, 3), dtype=np.int32)
+    for e in range(K):
+        R = frames[e]
+        for s in range(6):
+            l, sgn = s // 2, (-1 if s % 2 == 0 else 1)
+            step = R[:, l] * sgn  # outward lattice direction
+            nb_pos = lattice[e] + step
+            gdir = int(np.nonzero(step)[0][0])
+            if nb_pos[gdir] < 0 or nb_pos[gdir] >= dims[gdir]:
+                if not periodic[gdir]:
+                    face = 2 * gdir + (0 if step[gdir] < 0 else 1)
+                    conn[e, s] = (-1 - bc_ids[face], -1, 0)
+                    continue
+            nb_wrapped = nb_pos % dims
+            nb = index[tuple(nb_wrapped)]
+            Rn = frames[nb]
+            # neighbour side: outward direction opposite to ours
+            sn = None
+            for t in range(6):
+                ln, sgnn = t // 2, (-1 if t % 2 == 0 else 1)
+                if np.array_equal(Rn[:, ln] * sgnn, -step):
+                    sn = t
+                    break
+            # corner correspondence in lattice units (unwrapped neighbour box)
+            pmap = {}
+            for p, q in ((0, 0), (1, 0), (0, 1), (1, 1)):
+                xi = _face_corner_xi(s, p, q)
+                Lpt = lattice[e] + (R @ xi + 1) / 2.0
+                rel = Lpt - nb_pos
+                xin = Rn.T @ (2 * rel - 1)
+                ln = sn // 2
+                other = [d for d in range(3) if d != ln]
+                pmap[(p, q)] = (int(round((xin[other[0]] + 1) / 2)), int(round((xin[other[1]] + 1) / 2)))
+            conn[e, s] = (nb, sn, orientation_code(pmap))
+    # geometry at Ngeo LGL points in each element's local frame
+    r = lobatto_points(Ngeo)
+    kk, jj, ii = np.meshgrid(r, r, r, indexing="ij")
+    xi = np.stack([ii, jj, kk], axis=-1)
+    mesh = BoxMesh(nelem=tuple(nelem), Ngeo=Ngeo, coords=None, conn=conn, lattice=lattice, frames=frames,
+                   lo=lo, hi=hi, mapping=mapping)
+    mesh.coords = np.ascontiguousarray(mesh.map_points(xi))
+    return mesh
+
+
+def reorder_to_local(field_global_frame_fn, mesh: BoxMesh, N: int, node_type: int):
+    """Evaluate a pointwise field at each element's own node ordering."""
+    x = mesh.node_coords(N, node_type)
+    return field_global_frame_fn(x)
+
+
+# ----------------------------------------------------------------------------
+# initial states (nodal samples of closed-form fields); U layout [K, 5, n, n, n]
+# ----------------------------------------------------------------------------
+
+
+def prim_to_cons_np(rho, u, v, w, p, gamma):
+    E = p / (gamma - 1.0) + 0.5 * rho * (u * u + v * v + w * w)
+    return np.stack([rho, rho * u, rho * v, rho * w, E], axis=1)
+
+
+def taylor_green(x: np.ndarray, Ma: float = 0.1, gamma: float = 1.4, const_pressure: bool = False) -> np.ndarray:
+    """Taylor-Green vortex, V0 = L = rho0 = 1, p0 = 1/(gamma Ma^2)."""
+    X, Y, Z = x[:, 0], x[:, 1], x[:, 2]
+    u = np.sin(X) * np.cos(Y) * np.cos(Z)
+    v = -np.cos(X) * np.sin(Y) * np.cos(Z)
+    w = np.zeros_like(u)
+    p0 = 1.0 / (gamma * Ma * Ma)
+    if const_pressure:
+        p = np.full_like(u, p0)
+    else:
+        p = p0 + (np.cos(2 * X) + np.cos(2 * Y)) * (np.cos(2 * Z) + 2.0) / 16.0
+    rho = np.ones_like(u)
+    return prim_to_cons_np(rho, u, v, w, p, gamma)
+
+
+def freestream(x: np.ndarray, rho=1.0, vel=(0.3, 0.2, 0.1), p=None, gamma: float = 1.4) -> np.ndarray:
+    p = 1.0 / gamma if p is None else p
+    one = np.ones_like(x[:, 0])
+    return prim_to_cons_np(rho * one, vel[0] * one, vel[1] * one, vel[2] * one, p * one, gamma)
+
+
+def manufactured(x: np.ndarray, t: float = 0.0) -> np.ndarray:
+    """rho = 2 + 0.1 sin(pi (x+y+z-2t)), m = (rho, rho, rho), rho E = rho^2."""
+    rho = 2.0 + 0.1 * np.sin(np.pi * (x[:, 0] + x[:, 1] + x[:, 2] - 2.0 * t))
+    return np.stack([rho, rho, rho, rho, rho * rho], axis=1)
+
+
+def perturbed(x: np.ndarray, seed: int, amp: float = 0.05, Ma: float = 0.3, gamma: float = 1.4) -> np.ndarray:
+    """Smooth random state: a few seeded Fourier modes on top of a uniform flow.
+
+    Used where a generic (non-symmetric) state is wanted; periodic on [0, 2 pi]^3
+    for integer wave numbers.
+    """
+    rng = np.random.default_rng(seed)
+    X, Y, Z = x[:, 0], x[:, 1], x[:, 2]
+
+    def field():
+        f = np.zeros_like(X)
+        for _ in range(4):
+            kx, ky, kz = rng.integers(-2, 3, size=3)
+            ph = rng.uniform(0, 2 * np.pi)
+            a = rng.normal()
+            f = f + a * np.sin(kx * X + ky * Y + kz * Z + ph)
+        return f
+
+    rho = 1.0 + amp * field()
+    u = 0.3 + 3 * amp * field()
+    v = -0.2 + 3 * amp * field()
+    w = 0.1 + 3 * amp * field()
+    p = 1.0 / (gamma * Ma * Ma) * (1.0 + amp * field())
+    return prim_to_cons_np(rho, u, v, w, p, gamma)
+
+
+def random_directions(shape, count: int, seed0: int = 1910) -> list[np.ndarray]:
+    """Seeded unit-L2 random directions (N(0,1) per entry, then normalised)."""
+    out = []
+    for i in range(count):
+        rng = np.random.default_rng(seed0 + i)
+        v = rng.normal(size=shape)
+        out.append(v / np.linalg.norm(v))
+    return out
