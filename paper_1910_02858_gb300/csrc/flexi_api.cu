@@ -1,0 +1,648 @@
+// C-ABI layer of libflexi_gb300.so: context, mesh setup (connectivity and
+// FP64 geometry precompute), orchestration of the per-stage kernels, the RK
+// loop, reductions and kernel timing.  See include/flexi.h for the contract.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/flexi.h"
+#include "basis_host.h"
+#include "launch.h"
+
+using namespace flexi;
+
+namespace {
+
+// Carpenter & Kennedy (1994) five-stage fourth-order 2N-storage coefficients
+// (Williamson form, Sec. 3.4 names the scheme family; the paper prints none).
+const double RK_A[5] = {0.0, -567301805773.0 / 1357537059087.0, -2404267990393.0 / 2016746695238.0,
+                        -3550918686646.0 / 2091501179385.0, -1275806237668.0 / 842570457699.0};
+const double RK_B[5] = {1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
+                        1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
+                        2277821191437.0 / 14882151754819.0};
+const double RK_C[5] = {0.0, 1432997174477.0 / 9575080441755.0, 2526269341429.0 / 6820363962896.0,
+                        2006345519317.0 / 3224310063776.0, 2802321613138.0 / 2924317926251.0};
+
+enum { KC_LIFTVOL = 0, KC_FACE = 1, KC_SURF = 2, KC_PROLONG = 3, KC_BC = 4, KC_ADJ = 5, KC_RED = 6, KC_OTHER = 7 };
+
+}  // namespace
+
+struct flexi_ctx {
+  flexi_params p{};
+  int K = 0, N = 0, n = 0, n2 = 0, n3 = 0, S = 0, nBC = 0;
+  bool fp64 = true;
+  size_t rs = 8;
+  DevMesh m;
+  // FP64 geometry (always) and FP32 copies (FP32 forms)
+  double *Ja64 = nullptr, *sJ64 = nullptr, *wJ = nullptr, *xsol = nullptr, *fgeo64 = nullptr, *xbc = nullptr;
+  float *Ja32 = nullptr, *sJ32 = nullptr, *fgeo32 = nullptr;
+  int* elemSide = nullptr;
+  unsigned* status = nullptr;
+  double* partial = nullptr;
+  double* partial_host = nullptr;
+  int red_blocks = 0;
+  void *Ustate = nullptr, *dUstate = nullptr;
+  void* adj_scratch = nullptr;
+  Ops<double> ops64{};
+  Ops<float> ops32{};
+  Phys<double> ph64{};
+  Phys<float> ph32{};
+  SourceParams src{};
+  std::vector<void*> allocs;
+  size_t dev_bytes = 0;
+  // kernel timing
+  bool prof = false;
+  struct Rec { int cls; cudaEvent_t a, b; };
+  std::vector<Rec> pending;
+  double ms[8] = {0};
+  int64_t cnt[8] = {0};
+};
+
+namespace {
+
+flexi_status cuda_status(cudaError_t e) { return e == cudaSuccess ? FLEXI_OK : FLEXI_ECUDA; }
+
+#define CK(expr)                                   \
+  do {                                             \
+    cudaError_t _e = (expr);                       \
+    if (_e != cudaSuccess) return FLEXI_ECUDA;     \
+  } while (0)
+
+template <typename T>
+flexi_status dalloc(flexi_ctx* c, T** ptr, size_t count) {
+  void* p = nullptr;
+  const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+  if (cudaMalloc(&p, bytes) != cudaSuccess) return FLEXI_ENOMEM;
+  if (cudaMemset(p, 0, bytes) != cudaSuccess) return FLEXI_ECUDA;
+  c->allocs.push_back(p);
+  c->dev_bytes += bytes;
+  *ptr = static_cast<T*>(p);
+  return FLEXI_OK;
+}
+
+struct Prof {
+  flexi_ctx* c;
+  int cls;
+  cudaStream_t st;
+  cudaEvent_t a = nullptr, b = nullptr;
+  Prof(flexi_ctx* c_, int cls_, cudaStream_t st_) : c(c_), cls(cls_), st(st_) {
+    if (c->prof) {
+      cudaEventCreate(&a);
+      cudaEventCreate(&b);
+      cudaEventRecord(a, st);
+    }
+  }
+  ~Prof() {
+    if (c->prof) {
+      cudaEventRecord(b, st);
+      c->pending.push_back({cls, a, b});
+    }
+  }
+};
+
+void drain_profile(flexi_ctx* c) {
+  for (auto& r : c->pending) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+      c->ms[r.cls] += ms;
+      c->cnt[r.cls] += 1;
+    }
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  c->pending.clear();
+}
+
+template <typename real>
+const Ops<real>& ops_of(const flexi_ctx* c);
+template <>
+const Ops<double>& ops_of<double>(const flexi_ctx* c) { return c->ops64; }
+template <>
+const Ops<float>& ops_of<float>(const flexi_ctx* c) { return c->ops32; }
+template <typename real>
+const Phys<real>& ph_of(const flexi_ctx* c);
+template <>
+const Phys<double>& ph_of<double>(const flexi_ctx* c) { return c->ph64; }
+template <>
+const Phys<float>& ph_of<float>(const flexi_ctx* c) { return c->ph32; }
+
+// one evaluation of the operator up to (and excluding) the surface kernel
+template <typename real>
+flexi_status stage_front(flexi_ctx* c, const real* U, double t, bool prolong, int store_grad, cudaStream_t st) {
+  const Ops<real>& ops = ops_of<real>(c);
+  const Phys<real>& ph = ph_of<real>(c);
+  if (prolong) {
+    Prof pr(c, KC_PROLONG, st);
+    CK(launch_prolong<real>(c->m, U, ops, ph, st));
+  }
+  if (c->nBC > 0) {
+    Prof pr(c, KC_BC, st);
+    CK(launch_bc<real>(c->m, t, ph, st));
+  }
+  {
+    Prof pr(c, KC_LIFTVOL, st);
+    CK(launch_lift_vol<real>(c->m, U, ops, ph, store_grad, st));
+  }
+  {
+    Prof pr(c, KC_FACE, st);
+    CK(launch_face<real>(c->m, ph, st));
+  }
+  return FLEXI_OK;
+}
+
+template <typename real>
+flexi_status do_rhs(flexi_ctx* c, const real* U, real* Ut, double t, cudaStream_t st) {
+  flexi_status s = stage_front<real>(c, U, t, true, 0, st);
+  if (s != FLEXI_OK) return s;
+  RkStage<real> rk{real(0), real(0), real(0), 0};
+  Prof pr(c, KC_SURF, st);
+  CK(launch_surf<real>(c->m, 0, nullptr, nullptr, Ut, rk, t, c->src, ops_of<real>(c), ph_of<real>(c), st));
+  return FLEXI_OK;
+}
+
+template <typename real>
+flexi_status do_rk_step(flexi_ctx* c, real* U, real* dU, double t, double dt, real* stages, cudaStream_t st) {
+  const size_t nU = (size_t)c->K * NV * c->n3;
+  for (int k = 0; k < 5; ++k) {
+    const double tk = t + RK_C[k] * dt;
+    if (stages != nullptr) CK(cudaMemcpyAsync(stages + k * nU, U, nU * sizeof(real), cudaMemcpyDeviceToDevice, st));
+    flexi_status s = stage_front<real>(c, U, tk, k == 0, 0, st);
+    if (s != FLEXI_OK) return s;
+    RkStage<real> rk{(real)RK_A[k], (real)RK_B[k], (real)dt, k < 4 ? 1 : 0};
+    Prof pr(c, KC_SURF, st);
+    CK(launch_surf<real>(c->m, 1, U, dU, nullptr, rk, tk, c->src, ops_of<real>(c), ph_of<real>(c), st));
+  }
+  return FLEXI_OK;
+}
+
+template <typename real>
+void fill_ops(Ops<real>& o, const std::vector<double>& D, const std::vector<double>& w, const std::vector<double>& lm,
+              const std::vector<double>& lp, int n) {
+  std::memset(&o, 0, sizeof(o));
+  for (int i = 0; i < n; ++i)
+    for (int a = 0; a < n; ++a) {
+      const double dhat = -(w[a] / w[i]) * D[a * n + i];  // Dhat[i][a] = -(w_a/w_i) D_ai
+      o.DhatT[a * n + i] = (real)dhat;
+    }
+  for (int i = 0; i < n; ++i) {
+    o.lm[i] = (real)lm[i];
+    o.lp[i] = (real)lp[i];
+    o.lhm[i] = (real)(lm[i] / w[i]);
+    o.lhp[i] = (real)(lp[i] / w[i]);
+    o.w[i] = (real)w[i];
+  }
+}
+
+template <typename real>
+void fill_phys(Phys<real>& ph, const flexi_params& p) {
+  ph.gamma = (real)p.gamma;
+  ph.gm1 = (real)(p.gamma - 1.0);
+  ph.inv_gm1 = (real)(1.0 / (p.gamma - 1.0));
+  ph.mu = (real)p.mu;
+  ph.lam_th = (real)(p.mu * p.gamma / ((p.gamma - 1.0) * p.Pr));
+  ph.Ma = (real)p.Ma;
+  ph.riemann = p.riemann;
+  ph.bc_exact = p.bc_exact;
+}
+
+// orientation code composition helpers (host): T_o(p, q) on an n x n face
+void orient_host(int o, int N, int p, int q, int& pp, int& qq) {
+  const int a = (o & 1) ? q : p, b = (o & 1) ? p : q;
+  pp = (o & 2) ? N - a : a;
+  qq = (o & 4) ? N - b : b;
+}
+
+bool orient_inverse(int o, int oinv, int N) {
+  for (int q = 0; q <= N; ++q)
+    for (int p = 0; p <= N; ++p) {
+      int p1, q1, p2, q2;
+      orient_host(o, N, p, q, p1, q1);
+      orient_host(oinv, N, p1, q1, p2, q2);
+      if (p2 != p || q2 != q) return false;
+    }
+  return true;
+}
+
+flexi_status mesh_init_impl(flexi_ctx* c, const flexi_params* p, int K, const double* coords, const int32_t* conn,
+                            cudaStream_t st) {
+  c->p = *p;
+  c->K = K;
+  c->N = p->N;
+  c->n = p->N + 1;
+  c->n2 = c->n * c->n;
+  c->n3 = c->n2 * c->n;
+  c->fp64 = p->precision == FLEXI_FP64;
+  c->rs = c->fp64 ? sizeof(double) : sizeof(float);
+  const int N = c->N, n = c->n, n3 = c->n3, n2 = c->n2;
+  const int ng = p->Ngeo + 1, ng3 = ng * ng * ng;
+
+  // ---- sides (Sec. 5.1): boundary sides first, then inner sides; master = smaller (elem, side) key
+  std::vector<int> es(K * 6, -1);
+  std::vector<int> sideMaster;
+  std::vector<int> bnd_pairs, inner_pairs;  // (e, s)
+  for (int e = 0; e < K; ++e)
+    for (int s = 0; s < 6; ++s) {
+      const int nb = conn[(e * 6 + s) * 3 + 0], ns = conn[(e * 6 + s) * 3 + 1], o = conn[(e * 6 + s) * 3 + 2];
+      if (nb < 0) {
+        bnd_pairs.push_back(e * 6 + s);
+        continue;
+      }
+      if (nb >= K || ns < 0 || ns > 5 || o < 0 || o > 7) return FLEXI_EMESH;
+      const int bnb = conn[(nb * 6 + ns) * 3 + 0], bns = conn[(nb * 6 + ns) * 3 + 1], bo = conn[(nb * 6 + ns) * 3 + 2];
+      if (bnb != e || bns != s || !orient_inverse(o, bo, N)) return FLEXI_EMESH;
+      if (e * 6 + s < nb * 6 + ns) inner_pairs.push_back(e * 6 + s);
+    }
+  c->nBC = (int)bnd_pairs.size();
+  c->S = c->nBC + (int)inner_pairs.size();
+  sideMaster.resize(2 * c->S);
+  int sid = 0;
+  for (int key : bnd_pairs) {
+    const int e = key / 6, s = key % 6;
+    es[key] = (sid << 4);
+    sideMaster[2 * sid] = e;
+    sideMaster[2 * sid + 1] = s;
+    ++sid;
+  }
+  for (int key : inner_pairs) {
+    const int e = key / 6, s = key % 6;
+    const int nb = conn[key * 3 + 0], ns = conn[key * 3 + 1];
+    es[key] = (sid << 4);
+    es[nb * 6 + ns] = (sid << 4) | (1 << 3) | conn[(nb * 6 + ns) * 3 + 2];  // slave: its local -> master frame
+    sideMaster[2 * sid] = e;
+    sideMaster[2 * sid + 1] = s;
+    ++sid;
+  }
+  for (int v : es)
+    if (v < 0) return FLEXI_EMESH;
+  const int S = c->S;
+
+  // ---- host operators
+  std::vector<double> xs, ws, xl, wl, xg, wg;
+  if (p->node_type == FLEXI_NODES_GAUSS) host::gauss(N, xs, ws); else host::lobatto(N, xs, ws);
+  host::lobatto(N, xl, wl);
+  host::lobatto(p->Ngeo, xg, wg);
+  const std::vector<double> Ds = host::diff_matrix(xs), Dl = host::diff_matrix(xl);
+  const std::vector<double> Vg2l = host::interp_matrix(xg, xl), Vl2s = host::interp_matrix(xl, xs),
+                            Vg2s = host::interp_matrix(xg, xs);
+  const std::vector<double> lmv = host::interp_matrix(xs, {-1.0}), lpv = host::interp_matrix(xs, {1.0});
+  fill_ops<double>(c->ops64, Ds, ws, lmv, lpv, n);
+  fill_ops<float>(c->ops32, Ds, ws, lmv, lpv, n);
+  fill_phys<double>(c->ph64, *p);
+  fill_phys<float>(c->ph32, *p);
+  c->src.on = p->source;
+  c->src.gamma = p->gamma;
+  c->src.mu = p->mu;
+  c->src.Pr = p->Pr;
+
+  // ---- device buffers that live with the context
+  flexi_status s;
+#define AL(ptr, cnt) if ((s = dalloc(c, &(ptr), (cnt))) != FLEXI_OK) return s
+  AL(c->Ja64, (size_t)K * 9 * n3);
+  AL(c->sJ64, (size_t)K * n3);
+  AL(c->wJ, (size_t)K * n3);
+  AL(c->fgeo64, (size_t)S * 4 * n2);
+  AL(c->xbc, (size_t)std::max(c->nBC, 1) * 3 * n2);
+  AL(c->elemSide, (size_t)K * 6);
+  AL(c->status, 1);
+  if (p->source) AL(c->xsol, (size_t)K * 3 * n3);
+
+  // ---- temporary geometry buffers
+  std::vector<void*> tmp;
+  auto talloc = [&](double** ptr, size_t cnt) -> flexi_status {
+    void* q = nullptr;
+    if (cudaMalloc(&q, std::max<size_t>(cnt, 1) * sizeof(double)) != cudaSuccess) return FLEXI_ENOMEM;
+    tmp.push_back(q);
+    *ptr = (double*)q;
+    return FLEXI_OK;
+  };
+  auto free_tmp = [&]() { for (void* q : tmp) cudaFree(q); tmp.clear(); };
+  struct Guard { decltype(free_tmp)& f; ~Guard() { f(); } } guard{free_tmp};
+  double *X0, *A1, *A2, *XL, *dXL[3], *v, *dA, *dB, *JaL, *X, *dX[3], *dMat, *wdev;
+  int* sideM;
+#define TA(ptr, cnt) if ((s = talloc(&(ptr), (cnt))) != FLEXI_OK) return s
+  TA(X0, (size_t)K * 3 * ng3);
+  TA(A1, (size_t)K * 9 * n3);
+  TA(A2, (size_t)K * 9 * n3);
+  TA(XL, (size_t)K * 3 * n3);
+  for (int l = 0; l < 3; ++l) TA(dXL[l], (size_t)K * 3 * n3);
+  TA(v, (size_t)K * 9 * n3);
+  TA(dA, (size_t)K * n3);
+  TA(dB, (size_t)K * n3);
+  TA(JaL, (size_t)K * 9 * n3);
+  TA(X, (size_t)K * 3 * n3);
+  for (int l = 0; l < 3; ++l) TA(dX[l], (size_t)K * 3 * n3);
+  TA(dMat, 6 * 64 + 16);
+  TA(wdev, 16);
+  {
+    void* q = nullptr;
+    if (cudaMalloc(&q, sizeof(int) * 2 * std::max(S, 1)) != cudaSuccess) return FLEXI_ENOMEM;
+    tmp.push_back(q);
+    sideM = (int*)q;
+  }
+  // coordinates: [K][kg][jg][ig][3] -> [K][3][kg][jg][ig]
+  {
+    std::vector<double> h((size_t)K * 3 * ng3);
+    for (int e = 0; e < K; ++e)
+      for (int node = 0; node < ng3; ++node)
+        for (int d = 0; d < 3; ++d) h[((size_t)e * 3 + d) * ng3 + node] = coords[((size_t)e * ng3 + node) * 3 + d];
+    CK(cudaMemcpyAsync(X0, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+  }
+  // operator matrices on the device: Vg2l, Dl, Vl2s, Vg2s, Ds (each <= 64 entries)
+  double* dVg2l = dMat;
+  double* dDl = dMat + 64;
+  double* dVl2s = dMat + 128;
+  double* dVg2s = dMat + 192;
+  double* dDs = dMat + 256;
+  double* dlm = dMat + 320;
+  double* dlp = dMat + 328;
+  CK(cudaMemcpy(dVg2l, Vg2l.data(), Vg2l.size() * 8, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(dDl, Dl.data(), Dl.size() * 8, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(dVl2s, Vl2s.data(), Vl2s.size() * 8, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(dVg2s, Vg2s.data(), Vg2s.size() * 8, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(dDs, Ds.data(), Ds.size() * 8, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(dlm, lmv.data(), n * 8, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(dlp, lpv.data(), n * 8, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(wdev, ws.data(), n * 8, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(sideM, sideMaster.data(), sideMaster.size() * sizeof(int), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(c->elemSide, es.data(), es.size() * sizeof(int), cudaMemcpyHostToDevice));
+
+  // interpolate [B][m][m][m] -> [B][n][n][n] with matrix V (n x m)
+  auto interp3 = [&](const double* in, double* out, const double* V, int B, int m) -> cudaError_t {
+    cudaError_t e;
+    if ((e = geom_apply1d(in, A1, V, B, m, m, m, 0, n, st)) != cudaSuccess) return e;
+    if ((e = geom_apply1d(A1, A2, V, B, n, m, m, 1, n, st)) != cudaSuccess) return e;
+    return geom_apply1d(A2, out, V, B, n, n, m, 2, n, st);
+  };
+  // curl-form metrics on the degree-N Lobatto points (face metrics of the two
+  // elements of a side then agree), interpolated to the solution nodes
+  CK(interp3(X0, XL, dVg2l, 3 * K, ng));
+  for (int l = 0; l < 3; ++l) CK(geom_apply1d(XL, dXL[l], dDl, 3 * K, n, n, n, l, n, st));
+  CK(geom_metric_products(XL, dXL, v, K, n3, st));
+  const size_t blk = (size_t)K * n3;
+  for (int nn = 0; nn < 3; ++nn)
+    for (int i = 0; i < 3; ++i) {
+      const int i1 = (i + 1) % 3, i2 = (i + 2) % 3;
+      CK(geom_apply1d(v + (nn * 3 + i2) * blk, dA, dDl, K, n, n, n, i1, n, st));
+      CK(geom_apply1d(v + (nn * 3 + i1) * blk, dB, dDl, K, n, n, n, i2, n, st));
+      CK(geom_curl(dA, dB, JaL, K, n3, i, nn, st));
+    }
+  CK(interp3(JaL, c->Ja64, dVl2s, 9 * K, n));
+  // coordinates and Jacobian at the solution nodes
+  CK(interp3(X0, X, dVg2s, 3 * K, ng));
+  for (int l = 0; l < 3; ++l) CK(geom_apply1d(X, dX[l], dDs, 3 * K, n, n, n, l, n, st));
+  CK(geom_jacobian(dX, c->sJ64, c->wJ, wdev, K, n, c->status, st));
+  CK(geom_faces(c->Ja64, X, sideM, dlm, dlp, c->fgeo64, c->xbc, S, c->nBC, n, st));
+  if (p->source) CK(cudaMemcpyAsync(c->xsol, X, (size_t)K * 3 * n3 * 8, cudaMemcpyDeviceToDevice, st));
+  unsigned bad = 0;
+  CK(cudaMemcpyAsync(&bad, c->status, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (bad) return FLEXI_EMESH;
+  CK(cudaMemset(c->status, 0, sizeof(unsigned)));
+
+  // ---- arithmetic-form copies and scratch
+  c->m.K = K; c->m.S = S; c->m.nBC = c->nBC; c->m.N = N; c->m.n = n;
+  c->m.elemSide = c->elemSide;
+  c->m.xbc = c->xbc;
+  c->m.xsol = c->xsol;
+  c->m.status = c->status;
+  c->m.sweep_mode = p->precision == FLEXI_FP32_TF32 ? 1 : (p->precision == FLEXI_FP32_BF16 ? 2 : 0);
+  const size_t rs = c->rs;
+  if (c->fp64) {
+    c->m.Ja = c->Ja64; c->m.sJ = c->sJ64; c->m.fgeo = c->fgeo64;
+  } else {
+    AL(c->Ja32, (size_t)K * 9 * n3);
+    AL(c->sJ32, (size_t)K * n3);
+    AL(c->fgeo32, (size_t)S * 4 * n2);
+    CK(convert_f64_to_f32(c->Ja64, c->Ja32, (size_t)K * 9 * n3, st));
+    CK(convert_f64_to_f32(c->sJ64, c->sJ32, (size_t)K * n3, st));
+    CK(convert_f64_to_f32(c->fgeo64, c->fgeo32, (size_t)S * 4 * n2, st));
+    c->m.Ja = c->Ja32; c->m.sJ = c->sJ32; c->m.fgeo = c->fgeo32;
+  }
+  unsigned char *Wf, *Gf, *Ff, *Utv, *Us, *dUs;
+  AL(Wf, 2 * (size_t)S * NV * n2 * rs);
+  AL(Gf, 2 * (size_t)S * 15 * n2 * rs);
+  AL(Ff, (size_t)S * NV * n2 * rs);
+  AL(Utv, (size_t)K * NV * n3 * rs);
+  AL(Us, (size_t)K * NV * n3 * rs);
+  AL(dUs, (size_t)K * NV * n3 * rs);
+  c->m.Wf = Wf; c->m.Gf = Gf; c->m.Ff = Ff; c->m.Utv = Utv;
+  c->Ustate = Us; c->dUstate = dUs;
+  c->red_blocks = std::max(1, std::min(4 * 152, (int)(((size_t)K * n3 + 255) / 256)));
+  AL(c->partial, (size_t)c->red_blocks * kReduceQuantities);
+  if (cudaMallocHost(&c->partial_host, sizeof(double) * c->red_blocks * kReduceQuantities) != cudaSuccess)
+    return FLEXI_ENOMEM;
+  CK(cudaStreamSynchronize(st));
+#undef AL
+#undef TA
+  return FLEXI_OK;
+}
+
+template <typename real>
+flexi_status do_reduce(flexi_ctx* c, const void* U, const void* Ut, double cfl, double* out, cudaStream_t st) {
+  const double kv = std::max(4.0 / 3.0, c->p.gamma / c->p.Pr) * c->p.mu;
+  {
+    Prof pr(c, KC_RED, st);
+    CK(launch_reduce<real>((const real*)U, (const real*)Ut, c->wJ, c->Ja64, c->sJ64, (long long)c->K * c->n3, c->n3,
+                           ph_of<real>(c), kv, c->partial, c->red_blocks, st));
+  }
+  CK(cudaMemcpyAsync(c->partial_host, c->partial, sizeof(double) * c->red_blocks * kReduceQuantities,
+                     cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  double acc[kReduceQuantities] = {0};
+  for (int b = 0; b < c->red_blocks; ++b)
+    for (int q = 0; q < kReduceQuantities; ++q) {
+      const double val = c->partial_host[b * kReduceQuantities + q];
+      if (q < 7) acc[q] += val; else acc[q] = std::max(acc[q], val);
+    }
+  for (int q = 0; q < 7; ++q) out[q] = acc[q];
+  const int N = c->N;
+  const double dtc = cfl * 2.0 / ((2.0 * N + 1.0) * acc[7]);
+  const double dtv = acc[8] > 0 ? cfl * 4.0 / ((2.0 * N + 1.0) * acc[8]) : INFINITY;
+  out[7] = std::min(dtc, dtv);
+  return FLEXI_OK;
+}
+
+}  // namespace
+
+// ============================================================================
+// C ABI
+// ============================================================================
+extern "C" {
+
+const char* flexi_strerror(flexi_status s) {
+  switch (s) {
+    case FLEXI_OK: return "ok";
+    case FLEXI_EINVAL: return "invalid argument";
+    case FLEXI_ENOMEM: return "out of memory";
+    case FLEXI_ECUDA: return "CUDA runtime error";
+    case FLEXI_EMESH: return "invalid mesh (connectivity or non-positive Jacobian)";
+    case FLEXI_ENONPHYSICAL: return "non-physical state (rho <= 0 or p <= 0) detected";
+    case FLEXI_EUNSUPPORTED: return "unsupported configuration";
+  }
+  return "unknown status";
+}
+
+void flexi_destroy(flexi_ctx* c) {
+  if (c == nullptr) return;
+  cudaDeviceSynchronize();
+  for (auto& r : c->pending) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (void* p : c->allocs) cudaFree(p);
+  if (c->partial_host) cudaFreeHost(c->partial_host);
+  if (c->adj_scratch) cudaFree(c->adj_scratch);
+  delete c;
+}
+
+flexi_status flexi_mesh_init(flexi_ctx** out, const flexi_params* p, int K, const double* coords,
+                             const int32_t* conn, void* stream) {
+  if (out == nullptr || p == nullptr || coords == nullptr || conn == nullptr || K <= 0) return FLEXI_EINVAL;
+  *out = nullptr;
+  if (p->N < 1 || p->N > 7) return p->N > 7 ? FLEXI_EUNSUPPORTED : FLEXI_EINVAL;
+  if (p->Ngeo < 1 || p->Ngeo > p->N) return FLEXI_EINVAL;
+  if (p->node_type != FLEXI_NODES_GAUSS && p->node_type != FLEXI_NODES_LOBATTO) return FLEXI_EINVAL;
+  if (p->riemann < 0 || p->riemann > 2 || p->bc_exact < 0 || p->bc_exact > 2) return FLEXI_EINVAL;
+  if (p->precision < FLEXI_FP64 || p->precision > FLEXI_FP32_BF16) return FLEXI_EINVAL;
+  if (!(p->gamma > 1.0) || !(p->Pr > 0.0) || !(p->mu >= 0.0)) return FLEXI_EINVAL;
+  if ((long long)K * 6 >= (1LL << 27)) return FLEXI_EUNSUPPORTED;
+  flexi_ctx* c = new (std::nothrow) flexi_ctx();
+  if (c == nullptr) return FLEXI_ENOMEM;
+  const flexi_status s = mesh_init_impl(c, p, K, coords, conn, (cudaStream_t)stream);
+  if (s != FLEXI_OK) {
+    flexi_destroy(c);
+    return s;
+  }
+  *out = c;
+  return FLEXI_OK;
+}
+
+flexi_status flexi_rhs(flexi_ctx* c, const void* U, void* Ut, double t, void* stream) {
+  if (c == nullptr || U == nullptr || Ut == nullptr) return FLEXI_EINVAL;
+  if (c->m.sweep_mode != 0) return FLEXI_EUNSUPPORTED;
+  cudaStream_t st = (cudaStream_t)stream;
+  return c->fp64 ? do_rhs<double>(c, (const double*)U, (double*)Ut, t, st)
+                 : do_rhs<float>(c, (const float*)U, (float*)Ut, t, st);
+}
+
+flexi_status flexi_rk_step(flexi_ctx* c, void* U, void* dU, double t, double dt, void* stream) {
+  if (c == nullptr || U == nullptr || dU == nullptr) return FLEXI_EINVAL;
+  if (c->m.sweep_mode != 0) return FLEXI_EUNSUPPORTED;
+  cudaStream_t st = (cudaStream_t)stream;
+  return c->fp64 ? do_rk_step<double>(c, (double*)U, (double*)dU, t, dt, nullptr, st)
+                 : do_rk_step<float>(c, (float*)U, (float*)dU, t, dt, nullptr, st);
+}
+
+flexi_status flexi_rk_step_stages(flexi_ctx* c, void* U, void* dU, double t, double dt, void* U_stages,
+                                  void* stream) {
+  if (c == nullptr || U == nullptr || dU == nullptr || U_stages == nullptr) return FLEXI_EINVAL;
+  if (c->m.sweep_mode != 0) return FLEXI_EUNSUPPORTED;
+  cudaStream_t st = (cudaStream_t)stream;
+  return c->fp64 ? do_rk_step<double>(c, (double*)U, (double*)dU, t, dt, (double*)U_stages, st)
+                 : do_rk_step<float>(c, (float*)U, (float*)dU, t, dt, (float*)U_stages, st);
+}
+
+flexi_status flexi_adjoint_step(flexi_ctx* c, const void* U_stages, void* lamU, void* lam_dU, double t, double dt,
+                                void* stream) {
+  if (c == nullptr || U_stages == nullptr || lamU == nullptr || lam_dU == nullptr) return FLEXI_EINVAL;
+  return FLEXI_EUNSUPPORTED;
+}
+
+flexi_status flexi_rhs_adjoint(flexi_ctx* c, const void* U, const void* lam, void* out, double t, void* stream) {
+  if (c == nullptr || U == nullptr || lam == nullptr || out == nullptr) return FLEXI_EINVAL;
+  return FLEXI_EUNSUPPORTED;
+}
+
+flexi_status flexi_rk_run_host(flexi_ctx* c, void* U_host, int nsteps, double t0, double dt, void* stream) {
+  if (c == nullptr || U_host == nullptr || nsteps < 0) return FLEXI_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t bytes = (size_t)c->K * NV * c->n3 * c->rs;
+  CK(cudaMemcpyAsync(c->Ustate, U_host, bytes, cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(c->dUstate, 0, bytes, st));
+  for (int s = 0; s < nsteps; ++s) {
+    const flexi_status r = flexi_rk_step(c, c->Ustate, c->dUstate, t0 + s * dt, dt, stream);
+    if (r != FLEXI_OK) return r;
+  }
+  CK(cudaMemcpyAsync(U_host, c->Ustate, bytes, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return FLEXI_OK;
+}
+
+flexi_status flexi_reduce(flexi_ctx* c, const void* U, const void* Ut, double cfl, double* out, void* stream) {
+  if (c == nullptr || U == nullptr || out == nullptr) return FLEXI_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const flexi_status s = c->fp64 ? do_reduce<double>(c, U, Ut, cfl, out, st) : do_reduce<float>(c, U, Ut, cfl, out, st);
+  if (s != FLEXI_OK) return s;
+  unsigned flag = 0;
+  CK(cudaMemcpy(&flag, c->status, sizeof(unsigned), cudaMemcpyDeviceToHost));
+  if (flag) {
+    CK(cudaMemset(c->status, 0, sizeof(unsigned)));
+    return FLEXI_ENONPHYSICAL;
+  }
+  return FLEXI_OK;
+}
+
+flexi_status flexi_query(flexi_ctx* c, int what, int64_t* val) {
+  if (c == nullptr || val == nullptr) return FLEXI_EINVAL;
+  const double n = c->n, f = 3.0 / n;  // unique face nodes per volume node
+  const double dof = (double)c->K * c->n3;
+  switch (what) {
+    case FLEXI_Q_K: *val = c->K; return FLEXI_OK;
+    case FLEXI_Q_N: *val = c->N; return FLEXI_OK;
+    case FLEXI_Q_NSIDES: *val = c->S; return FLEXI_OK;
+    case FLEXI_Q_NBCSIDES: *val = c->nBC; return FLEXI_OK;
+    case FLEXI_Q_DOF: *val = (int64_t)dof; return FLEXI_OK;
+    case FLEXI_Q_BYTES_PER_STAGE: {
+      // minimum-traffic three-kernel schedule, words per DOF: 46 + 117 f
+      *val = (int64_t)((46.0 + 117.0 * f) * dof * c->rs);
+      return FLEXI_OK;
+    }
+    case FLEXI_Q_FLOPS_PER_STAGE: {
+      // per DOF: D_hat sweeps 2*(45+15) n; LG prolongation of U and grad U and the
+      // two surface integrals 2*(4*6*20)/... see DESIGN; pointwise ~100; faces 300 f; RK 4
+      const bool lg = c->p.node_type == FLEXI_NODES_GAUSS;
+      const double sweeps = 2.0 * 60.0 * n;
+      const double surf = lg ? 2.0 * (6 * 5 + 6 * 15 + 6 * 5 + 6 * 15) : 2.0 * (6 * 5 + 6 * 15) * (1.0 / n) * 2;
+      const double transform = 2.0 * 90.0;
+      *val = (int64_t)((sweeps + surf + transform + 100.0 + 300.0 * f + 4.0) * dof);
+      return FLEXI_OK;
+    }
+    case FLEXI_Q_STATUS: {
+      unsigned flag = 0;
+      CK(cudaMemcpy(&flag, c->status, sizeof(unsigned), cudaMemcpyDeviceToHost));
+      CK(cudaMemset(c->status, 0, sizeof(unsigned)));
+      *val = flag;
+      return FLEXI_OK;
+    }
+    case FLEXI_Q_DEVICE_BYTES: *val = (int64_t)c->dev_bytes; return FLEXI_OK;
+    case FLEXI_Q_PRECISION: *val = c->p.precision; return FLEXI_OK;
+  }
+  return FLEXI_EINVAL;
+}
+
+flexi_status flexi_profile(flexi_ctx* c, int enable) {
+  if (c == nullptr) return FLEXI_EINVAL;
+  c->prof = enable != 0;
+  return FLEXI_OK;
+}
+
+flexi_status flexi_kernel_times(flexi_ctx* c, double* ms, int64_t* count, int reset) {
+  if (c == nullptr) return FLEXI_EINVAL;
+  drain_profile(c);
+  for (int k = 0; k < 8; ++k) {
+    if (ms) ms[k] = c->ms[k];
+    if (count) count[k] = c->cnt[k];
+    if (reset) {
+      c->ms[k] = 0;
+      c->cnt[k] = 0;
+    }
+  }
+  return FLEXI_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,528 @@
+// Forward DGSEM kernels (templated on the arithmetic type and on n = N + 1).
+//
+// Per RK stage (Sec. 5.5 algorithm sequence, re-scheduled for one GPU):
+//   k_prolong   element kernel: U -> primitive face states W(U_face) (a1)
+//   k_bc        boundary sides: Dirichlet state in the outer slot
+//   k_lift_vol  element kernel: BR1 lifting (a2, a3, Eq. discreteGradient),
+//               gradients to the faces (a4), volume fluxes + contravariant
+//               transform (a6) and the D_hat volume integral (a7)
+//   k_face      side kernel: Riemann + BR1 viscous flux times s_hat (a5)
+//   k_surf      element kernel: surface integral (a8), -1/J scaling (a9), the
+//               low-storage RK update (a10) and the face states of the new U
+//
+// One thread per volume node; NE elements per CTA so that a CTA has >= 64
+// threads for small n.  Line sweeps of D_hat read the element's staged fields
+// from shared memory; the per-node results stay in registers.
+#pragma once
+#include "dg_common.cuh"
+#include "launch.h"
+
+namespace flexi {
+
+template <int n>
+struct Cfg {
+  static constexpr int n2 = n * n;
+  static constexpr int n3 = n * n * n;
+  static constexpr int NE = n3 >= 64 ? 1 : (64 + n3 - 1) / n3;
+  static constexpr int T = NE * n3;
+};
+
+// shared copy of the 1-D operators: DhatT[n*n], lm, lp, lhm, lhp
+template <typename real, int n>
+__device__ __forceinline__ void load_ops(real* s, const Ops<real>& ops, int tid, int T) {
+  for (int t = tid; t < n * n; t += T) s[t] = ops.DhatT[t];
+  for (int t = tid; t < n; t += T) {
+    s[n * n + t] = ops.lm[t];
+    s[n * n + n + t] = ops.lp[t];
+    s[n * n + 2 * n + t] = ops.lhm[t];
+    s[n * n + 3 * n + t] = ops.lhp[t];
+  }
+}
+
+// sum_a Dhat[i][a] f0[a,j,k] + Dhat[j][a] f1[i,a,k] + Dhat[k][a] f2[i,j,a] for NV fields each
+template <typename real, int n>
+__device__ __forceinline__ void dhat_sweep3(const real* __restrict__ sD, const real* __restrict__ buf, int i, int j,
+                                            int k, real acc[NV]) {
+  constexpr int n2 = n * n, n3 = n * n * n;
+#pragma unroll
+  for (int a = 0; a < n; ++a) {
+    const real d0 = sD[a * n + i], d1 = sD[a * n + j], d2 = sD[a * n + k];
+    const int i0 = a + n * j + n2 * k, i1 = i + n * a + n2 * k, i2 = i + n * j + n2 * a;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      acc[v] += d0 * buf[v * n3 + i0];
+      acc[v] += d1 * buf[(NV + v) * n3 + i1];
+      acc[v] += d2 * buf[(2 * NV + v) * n3 + i2];
+    }
+  }
+}
+
+// Face states of U (staged in shared memory as sU[el][5][n3]) for all six
+// faces of every element of the CTA: W(U_face) written to the side arrays.
+template <typename real, int n>
+__device__ __forceinline__ void faces_from_volume(const real* __restrict__ sU, const real* __restrict__ sOp,
+                                                  const int* __restrict__ sES, int e0, int K, int S,
+                                                  real* __restrict__ Wf, const Phys<real>& ph,
+                                                  unsigned* __restrict__ status, int tid) {
+  using C = Cfg<n>;
+  constexpr int n2 = C::n2, n3 = C::n3;
+  const real* lm = sOp + n2;
+  const real* lp = sOp + n2 + n;
+  for (int it = tid; it < C::NE * 6 * n2; it += C::T) {
+    const int el = it / (6 * n2);
+    const int r = it - el * 6 * n2;
+    const int s = r / n2, pq = r - s * n2;
+    const int e = e0 + el;
+    if (e >= K) continue;
+    const int l = s >> 1;
+    const real* lv = (s & 1) ? lp : lm;
+    const int p = pq % n, q = pq / n;
+    real Uf[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Uf[v] = real(0);
+#pragma unroll
+    for (int a = 0; a < n; ++a) {
+      const real c = lv[a];
+      const int vi = vol_index(l, a, p, q, n);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) Uf[v] += c * sU[(el * NV + v) * n3 + vi];
+    }
+    real W[NV];
+    cons_to_prim(Uf, W, ph);
+    if (!(W[0] > real(0)) || !(W[4] > real(0))) atomicOr(status, 1u);
+    const int es = sES[el * 6 + s];
+    const int side = es_side(es), slot = es_slave(es);
+    const int mpq = orient_pq(es_orient(es), n - 1, p, q);
+    real* dst = Wf + ((size_t)(slot * S + side) * NV) * n2 + mpq;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) dst[v * n2] = W[v];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// a1: prolongation of U to the faces (primitive face states)
+// ---------------------------------------------------------------------------
+template <typename real, int n>
+__global__ void __launch_bounds__(Cfg<n>::T) k_prolong(const real* __restrict__ U, const int* __restrict__ elemSide,
+                                                        real* __restrict__ Wf, int K, int S, Ops<real> ops,
+                                                        Phys<real> ph, unsigned* __restrict__ status) {
+  using C = Cfg<n>;
+  constexpr int n3 = C::n3;
+  __shared__ real sU[C::NE * NV * n3];
+  __shared__ real sOp[n * n + 4 * n];
+  __shared__ int sES[C::NE * 6];
+  const int tid = threadIdx.x;
+  const int e0 = blockIdx.x * C::NE;
+  load_ops<real, n>(sOp, ops, tid, C::T);
+  for (int t = tid; t < C::NE * 6; t += C::T) sES[t] = (e0 + t / 6 < K) ? elemSide[(size_t)e0 * 6 + t] : 0;
+  for (int t = tid; t < C::NE * NV * n3; t += C::T)
+    sU[t] = (e0 + t / (NV * n3) < K) ? U[(size_t)e0 * NV * n3 + t] : real(1);
+  __syncthreads();
+  faces_from_volume<real, n>(sU, sOp, sES, e0, K, S, Wf, ph, status, tid);
+}
+
+// ---------------------------------------------------------------------------
+// Dirichlet boundary sides: outer state = exact state at the face nodes
+// ---------------------------------------------------------------------------
+template <typename real, int n>
+__global__ void k_bc(const double* __restrict__ xbc, real* __restrict__ Wf, int S, int nBC, double t,
+                     Phys<real> ph) {
+  constexpr int n2 = n * n;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nBC * n2) return;
+  const int b = idx / n2, pq = idx - b * n2;
+  double x[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) x[c] = xbc[((size_t)b * 3 + c) * n2 + pq];
+  real U[NV], W[NV];
+  exact_state<real>(ph.bc_exact, x, t, ph, U);
+  cons_to_prim(U, W, ph);
+  real* dst = Wf + ((size_t)(S + b) * NV) * n2 + pq;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) dst[v * n2] = W[v];
+}
+
+// ---------------------------------------------------------------------------
+// a2-a4, a6, a7: lifting, gradient prolongation, volume integral
+// ---------------------------------------------------------------------------
+template <typename real, int n>
+__global__ void __launch_bounds__(Cfg<n>::T) k_lift_vol(
+    const real* __restrict__ U, const real* __restrict__ Ja, const real* __restrict__ sJ,
+    const real* __restrict__ Wf, const real* __restrict__ fgeo, const int* __restrict__ elemSide,
+    real* __restrict__ Gf, real* __restrict__ Utv, real* __restrict__ Gvol, int K, int S, Ops<real> ops,
+    Phys<real> ph) {
+  using C = Cfg<n>;
+  constexpr int n2 = C::n2, n3 = C::n3, NE = C::NE, T = C::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  real* sbuf = reinterpret_cast<real*>(smem_raw);  // [NE][15][n3]
+  real* sQ = sbuf + NE * 15 * n3;                  // [NE][6][15][n2]  (v*3+d)
+  real* sOp = sQ + NE * 6 * 15 * n2;               // DhatT, lm, lp, lhm, lhp
+  int* sES = reinterpret_cast<int*>(sOp + n2 + 4 * n);
+
+  const int tid = threadIdx.x;
+  const int el = tid / n3, node = tid - el * n3;
+  const int e0 = blockIdx.x * NE;
+  const int e = e0 + el;
+  const bool valid = e < K;
+  const int i = node % n, j = (node / n) % n, k = node / n2;
+
+  load_ops<real, n>(sOp, ops, tid, T);
+  for (int t = tid; t < NE * 6; t += T) sES[t] = (e0 + t / 6 < K) ? elemSide[(size_t)e0 * 6 + t] : 0;
+
+  real Uo[NV], W[NV], jac[9], sj;
+  if (valid) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Uo[v] = U[((size_t)e * NV + v) * n3 + node];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) jac[c] = Ja[((size_t)e * 9 + c) * n3 + node];
+    sj = sJ[(size_t)e * n3 + node];
+  } else {
+    Uo[0] = real(1); Uo[1] = Uo[2] = Uo[3] = real(0); Uo[4] = real(1);
+#pragma unroll
+    for (int c = 0; c < 9; ++c) jac[c] = real(0);
+    sj = real(0);
+  }
+  cons_to_prim(Uo, W, ph);
+  __syncthreads();
+
+  // BR1 surface terms: Q = U* n_d s_hat with the element's outward normal
+  for (int it = tid; it < NE * 6 * n2; it += T) {
+    const int el2 = it / (6 * n2);
+    const int r = it - el2 * 6 * n2;
+    const int s = r / n2, pq = r - s * n2;
+    if (e0 + el2 >= K) continue;
+    const int es = sES[el2 * 6 + s];
+    const int side = es_side(es);
+    const int mpq = orient_pq(es_orient(es), n - 1, pq % n, pq / n);
+    const real* w0 = Wf + ((size_t)side * NV) * n2 + mpq;
+    const real* w1 = Wf + ((size_t)(S + side) * NV) * n2 + mpq;
+    const real* g = fgeo + ((size_t)side * 4) * n2 + mpq;
+    const real sc = es_slave(es) ? -g[3 * n2] : g[3 * n2];
+    const real nd[3] = {g[0] * sc, g[n2] * sc, g[2 * n2] * sc};
+    real* Q = sQ + ((el2 * 6 + s) * 15) * n2 + pq;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const real ws = real(0.5) * (w0[v * n2] + w1[v * n2]);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) Q[(v * 3 + d) * n2] = ws * nd[d];
+    }
+  }
+
+  real G[15];
+  real* myb = sbuf + el * 15 * n3;
+  const real* sD = sOp;
+  const real* lhm = sOp + n2 + 2 * n;
+  const real* lhp = sOp + n2 + 3 * n;
+  const real* Qe = sQ + el * 6 * 15 * n2;
+  const int pq0 = j + n * k, pq1 = i + n * k, pq2 = i + n * j;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    __syncthreads();
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+      const real a = jac[l * 3 + d];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) myb[(l * NV + v) * n3 + node] = a * W[v];
+    }
+    __syncthreads();
+    real acc[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[v] = real(0);
+    dhat_sweep3<real, n>(sD, myb, i, j, k, acc);
+    const real c0 = lhm[i], c1 = lhp[i], c2 = lhm[j], c3 = lhp[j], c4 = lhm[k], c5 = lhp[k];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const int o = (v * 3 + d) * n2;
+      acc[v] += c0 * Qe[0 * 15 * n2 + o + pq0] + c1 * Qe[1 * 15 * n2 + o + pq0];
+      acc[v] += c2 * Qe[2 * 15 * n2 + o + pq1] + c3 * Qe[3 * 15 * n2 + o + pq1];
+      acc[v] += c4 * Qe[4 * 15 * n2 + o + pq2] + c5 * Qe[5 * 15 * n2 + o + pq2];
+      G[d * NV + v] = acc[v] * sj;
+    }
+  }
+
+  // a4: gradients to the faces
+  __syncthreads();
+#pragma unroll
+  for (int c = 0; c < 15; ++c) myb[c * n3 + node] = G[c];
+  if (Gvol != nullptr && valid) {
+#pragma unroll
+    for (int c = 0; c < 15; ++c) Gvol[((size_t)e * 15 + c) * n3 + node] = G[c];
+  }
+  __syncthreads();
+  {
+    const real* lm = sOp + n2;
+    const real* lp = sOp + n2 + n;
+    for (int it = tid; it < NE * 6 * 15 * n2; it += T) {
+      const int el2 = it / (6 * 15 * n2);
+      int r = it - el2 * 6 * 15 * n2;
+      const int s = r / (15 * n2);
+      r -= s * 15 * n2;
+      const int c = r / n2, pq = r - c * n2;
+      if (e0 + el2 >= K) continue;
+      const int l = s >> 1;
+      const real* lv = (s & 1) ? lp : lm;
+      const int p = pq % n, q = pq / n;
+      const real* b = sbuf + (el2 * 15 + c) * n3;
+      real val = real(0);
+#pragma unroll
+      for (int a = 0; a < n; ++a) val += lv[a] * b[vol_index(l, a, p, q, n)];
+      const int es = sES[el2 * 6 + s];
+      const int mpq = orient_pq(es_orient(es), n - 1, p, q);
+      Gf[((size_t)(es_slave(es) * S + es_side(es)) * 15 + c) * n2 + mpq] = val;
+    }
+  }
+  __syncthreads();
+
+  // a6: contravariant fluxes Fcal^l = sum_d Ja^l_d (F^c_d - F^v_d), accumulated in shared memory
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    real F[NV];
+    flux_total(Uo, W, G, d, ph, F);
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+      const real a = jac[l * 3 + d];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        real* dst = &myb[(l * NV + v) * n3 + node];
+        *dst = (d == 0 ? real(0) : *dst) + a * F[v];
+      }
+    }
+  }
+  __syncthreads();
+  // a7: volume integral
+  real acc[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) acc[v] = real(0);
+  dhat_sweep3<real, n>(sD, myb, i, j, k, acc);
+  if (valid) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Utv[((size_t)e * NV + v) * n3 + node] = acc[v];
+  }
+}
+
+template <typename real, int n>
+constexpr size_t lift_vol_smem() {
+  using C = Cfg<n>;
+  return sizeof(real) * (C::NE * 15 * C::n3 + C::NE * 6 * 15 * C::n2 + C::n2 + 4 * n) + sizeof(int) * C::NE * 6;
+}
+
+// ---------------------------------------------------------------------------
+// a5: numerical flux on every side (master normal)
+// ---------------------------------------------------------------------------
+template <typename real, int n>
+__global__ void __launch_bounds__(128) k_face(const real* __restrict__ Wf, const real* __restrict__ Gf,
+                                              const real* __restrict__ fgeo, real* __restrict__ Ff, int S, int nBC,
+                                              Phys<real> ph) {
+  constexpr int n2 = n * n;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= S * n2) return;
+  const int side = idx / n2, pq = idx - side * n2;
+  real WL[NV], WR[NV], GL[15], GR[15], nv[3];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    WL[v] = Wf[((size_t)side * NV + v) * n2 + pq];
+    WR[v] = Wf[((size_t)(S + side) * NV + v) * n2 + pq];
+  }
+  const bool bnd = side < nBC;
+#pragma unroll
+  for (int c = 0; c < 15; ++c) {
+    GL[c] = Gf[((size_t)side * 15 + c) * n2 + pq];
+    GR[c] = bnd ? GL[c] : Gf[((size_t)(S + side) * 15 + c) * n2 + pq];
+  }
+#pragma unroll
+  for (int d = 0; d < 3; ++d) nv[d] = fgeo[((size_t)side * 4 + d) * n2 + pq];
+  const real sa = fgeo[((size_t)side * 4 + 3) * n2 + pq];
+  real f[NV], fl[NV], fr[NV];
+  riemann(WL, WR, nv, ph, f);
+  visc_normal(WL, GL, nv, ph, fl);
+  visc_normal(WR, GR, nv, ph, fr);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) Ff[((size_t)side * NV + v) * n2 + pq] = (f[v] - real(0.5) * (fl[v] + fr[v])) * sa;
+}
+
+// ---------------------------------------------------------------------------
+// a8-a10: surface integral, -1/J, RK stage update, face states of the new U
+// ---------------------------------------------------------------------------
+template <typename real, int n, int MODE>
+__global__ void __launch_bounds__(Cfg<n>::T) k_surf(
+    const real* __restrict__ Ff, const int* __restrict__ elemSide, const real* __restrict__ sJ,
+    const real* __restrict__ Utv, real* __restrict__ U, real* __restrict__ dU, real* __restrict__ Ut,
+    real* __restrict__ Wf, const double* __restrict__ xsol, RkStage<real> rk, double t, SourceParams src, int K,
+    int S, Ops<real> ops, Phys<real> ph, unsigned* __restrict__ status) {
+  using C = Cfg<n>;
+  constexpr int n2 = C::n2, n3 = C::n3, NE = C::NE, T = C::T;
+  __shared__ real sF[NE * 6 * NV * n2];
+  __shared__ real sU[(MODE == 1) ? NE * NV * n3 : 1];
+  __shared__ real sOp[n2 + 4 * n];
+  __shared__ int sES[NE * 6];
+  const int tid = threadIdx.x;
+  const int el = tid / n3, node = tid - el * n3;
+  const int e0 = blockIdx.x * NE;
+  const int e = e0 + el;
+  const bool valid = e < K;
+  const int i = node % n, j = (node / n) % n, k = node / n2;
+  load_ops<real, n>(sOp, ops, tid, T);
+  for (int t2 = tid; t2 < NE * 6; t2 += T) sES[t2] = (e0 + t2 / 6 < K) ? elemSide[(size_t)e0 * 6 + t2] : 0;
+  __syncthreads();
+  for (int it = tid; it < NE * 6 * n2; it += T) {
+    const int el2 = it / (6 * n2);
+    const int r = it - el2 * 6 * n2;
+    const int s = r / n2, pq = r - s * n2;
+    if (e0 + el2 >= K) continue;
+    const int es = sES[el2 * 6 + s];
+    const int mpq = orient_pq(es_orient(es), n - 1, pq % n, pq / n);
+    const real sg = es_slave(es) ? real(-1) : real(1);
+    const real* src_f = Ff + ((size_t)es_side(es) * NV) * n2 + mpq;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) sF[((el2 * 6 + s) * NV + v) * n2 + pq] = sg * src_f[v * n2];
+  }
+  __syncthreads();
+  real ut[NV];
+  if (valid) {
+    const real* lhm = sOp + n2 + 2 * n;
+    const real* lhp = sOp + n2 + 3 * n;
+    const real c0 = lhm[i], c1 = lhp[i], c2 = lhm[j], c3 = lhp[j], c4 = lhm[k], c5 = lhp[k];
+    const int pq0 = j + n * k, pq1 = i + n * k, pq2 = i + n * j;
+    const real* Fe = sF + el * 6 * NV * n2;
+    const real sj = sJ[(size_t)e * n3 + node];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      real s = Utv[((size_t)e * NV + v) * n3 + node];
+      s += c0 * Fe[(0 * NV + v) * n2 + pq0] + c1 * Fe[(1 * NV + v) * n2 + pq0];
+      s += c2 * Fe[(2 * NV + v) * n2 + pq1] + c3 * Fe[(3 * NV + v) * n2 + pq1];
+      s += c4 * Fe[(4 * NV + v) * n2 + pq2] + c5 * Fe[(5 * NV + v) * n2 + pq2];
+      ut[v] = -s * sj;
+    }
+    if (src.on) {
+      double x[3], Sv[NV];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) x[c] = xsol[((size_t)e * 3 + c) * n3 + node];
+      manufactured_source(x, t, src.gamma, src.mu, src.Pr, Sv);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) ut[v] += (real)Sv[v];
+    }
+  }
+  if (MODE == 0) {
+    if (valid) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) Ut[((size_t)e * NV + v) * n3 + node] = ut[v];
+    }
+    return;
+  } else {
+    if (valid) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const size_t g = ((size_t)e * NV + v) * n3 + node;
+        const real du = rk.A * dU[g] + rk.dt * ut[v];
+        const real un = U[g] + rk.B * du;
+        dU[g] = du;
+        U[g] = un;
+        sU[(el * NV + v) * n3 + node] = un;
+      }
+    } else {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) sU[(el * NV + v) * n3 + node] = (v == 0 || v == 4) ? real(1) : real(0);
+    }
+    if (rk.prolong) {
+      __syncthreads();
+      faces_from_volume<real, n>(sU, sOp, sES, e0, K, S, Wf, ph, status, tid);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+#define FLEXI_DISPATCH_N(nval, ...) \
+  switch (nval) {                    \
+    case 2: { constexpr int NN = 2; __VA_ARGS__; } break; \
+    case 3: { constexpr int NN = 3; __VA_ARGS__; } break; \
+    case 4: { constexpr int NN = 4; __VA_ARGS__; } break; \
+    case 5: { constexpr int NN = 5; __VA_ARGS__; } break; \
+    case 6: { constexpr int NN = 6; __VA_ARGS__; } break; \
+    case 7: { constexpr int NN = 7; __VA_ARGS__; } break; \
+    case 8: { constexpr int NN = 8; __VA_ARGS__; } break; \
+    default: return cudaErrorInvalidValue;         \
+  }
+
+template <typename real, int n>
+static cudaError_t prolong_n(const DevMesh& m, const real* U, const Ops<real>& ops, const Phys<real>& ph,
+                             cudaStream_t st) {
+  using C = Cfg<n>;
+  const int grid = (m.K + C::NE - 1) / C::NE;
+  k_prolong<real, n><<<grid, C::T, 0, st>>>(U, m.elemSide, (real*)m.Wf, m.K, m.S, ops, ph, m.status);
+  return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t launch_prolong(const DevMesh& m, const real* U, const Ops<real>& ops, const Phys<real>& ph,
+                           cudaStream_t st) {
+  FLEXI_DISPATCH_N(m.n, return prolong_n<real, NN>(m, U, ops, ph, st));
+  return cudaSuccess;
+}
+
+template <typename real>
+cudaError_t launch_bc(const DevMesh& m, double t, const Phys<real>& ph, cudaStream_t st) {
+  if (m.nBC == 0) return cudaSuccess;
+  const int tot = m.nBC * m.n * m.n;
+  FLEXI_DISPATCH_N(m.n, (k_bc<real, NN><<<(tot + 127) / 128, 128, 0, st>>>(m.xbc, (real*)m.Wf, m.S, m.nBC, t, ph)));
+  return cudaGetLastError();
+}
+
+template <typename real, int n>
+static cudaError_t lift_vol_n(const DevMesh& m, const real* U, const Ops<real>& ops, const Phys<real>& ph,
+                              int store_grad, cudaStream_t st) {
+  using C = Cfg<n>;
+  constexpr size_t smem = lift_vol_smem<real, n>();
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t err = cudaFuncSetAttribute(k_lift_vol<real, n>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    attr = true;
+  }
+  const int grid = (m.K + C::NE - 1) / C::NE;
+  k_lift_vol<real, n><<<grid, C::T, smem, st>>>(U, (const real*)m.Ja, (const real*)m.sJ, (const real*)m.Wf,
+                                                (const real*)m.fgeo, m.elemSide, (real*)m.Gf, (real*)m.Utv,
+                                                store_grad ? (real*)m.Gvol : nullptr, m.K, m.S, ops, ph);
+  return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t launch_lift_vol(const DevMesh& m, const real* U, const Ops<real>& ops, const Phys<real>& ph,
+                            int store_grad, cudaStream_t st) {
+  FLEXI_DISPATCH_N(m.n, return lift_vol_n<real, NN>(m, U, ops, ph, store_grad, st));
+  return cudaSuccess;
+}
+
+template <typename real>
+cudaError_t launch_face(const DevMesh& m, const Phys<real>& ph, cudaStream_t st) {
+  const int tot = m.S * m.n * m.n;
+  FLEXI_DISPATCH_N(m.n, (k_face<real, NN><<<(tot + 127) / 128, 128, 0, st>>>(
+                            (const real*)m.Wf, (const real*)m.Gf, (const real*)m.fgeo, (real*)m.Ff, m.S, m.nBC, ph)));
+  return cudaGetLastError();
+}
+
+template <typename real, int n>
+static cudaError_t surf_n(const DevMesh& m, int mode, real* U, real* dU, real* Ut, const RkStage<real>& rk, double t,
+                          const SourceParams& src, const Ops<real>& ops, const Phys<real>& ph, cudaStream_t st) {
+  using C = Cfg<n>;
+  const int grid = (m.K + C::NE - 1) / C::NE;
+  if (mode == 0)
+    k_surf<real, n, 0><<<grid, C::T, 0, st>>>((const real*)m.Ff, m.elemSide, (const real*)m.sJ,
+                                              (const real*)m.Utv, U, dU, Ut, (real*)m.Wf, m.xsol, rk, t, src, m.K,
+                                              m.S, ops, ph, m.status);
+  else
+    k_surf<real, n, 1><<<grid, C::T, 0, st>>>((const real*)m.Ff, m.elemSide, (const real*)m.sJ,
+                                              (const real*)m.Utv, U, dU, Ut, (real*)m.Wf, m.xsol, rk, t, src, m.K,
+                                              m.S, ops, ph, m.status);
+  return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t launch_surf(const DevMesh& m, int mode, real* U, real* dU, real* Ut, const RkStage<real>& rk, double t,
+                        const SourceParams& src, const Ops<real>& ops, const Phys<real>& ph, cudaStream_t st) {
+  FLEXI_DISPATCH_N(m.n, return surf_n<real, NN>(m, mode, U, dU, Ut, rk, t, src, ops, ph, st));
+  return cudaSuccess;
+}
+
+}  // namespace flexi

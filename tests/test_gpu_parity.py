@@ -1,0 +1,260 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances (derived in the design notes): the right-hand side is a sum of
+terms whose magnitude is set by the volume integral, so its rounding error is
+bounded relative to ||vol/J|| per variable; the FP64 bar is 1e-12 relative in
+that scale, and 1e-12 relative L2 per conserved variable for states after
+time steps (the spec bar for the FP64 path).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import workloads as wl
+from oracle import equations as eq
+from oracle.dgsem import DGSEM, HLLC, ROE, Params
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1910_02858_gb300 import build as b
+
+    b.build()
+    from paper_1910_02858_gb300 import flexi as F
+
+    F.lib()
+
+
+def _solver(cfg_kw, mesh):
+    from paper_1910_02858_gb300 import Solver, SolverConfig
+
+    return Solver(SolverConfig(**cfg_kw), mesh.coords, mesh.conn, device=DEV)
+
+
+def _oracle(cfg_kw, mesh):
+    r = {0: ROE, 1: HLLC, 2: ROE}[cfg_kw.get("riemann", 0)]
+    bc = cfg_kw.get("bc_exact", 0)
+    return DGSEM(Params(N=cfg_kw["N"], node_type=cfg_kw.get("node_type", 0), riemann=r,
+                        smooth_roe=cfg_kw.get("riemann", 0) == 2, mu=cfg_kw.get("mu", 1 / 1600.0),
+                        Ma=cfg_kw.get("Ma", 0.1), bc_exact=bc, source=cfg_kw.get("source", False),
+                        gamma=cfg_kw.get("gamma", 1.4), Pr=cfg_kw.get("Pr", 0.72)), mesh.coords, mesh.conn)
+
+
+def per_var_rel(a, b, scale=None):
+    a, b = a.double().cpu(), b.double().cpu()
+    d = (a - b).transpose(0, 1).reshape(5, -1).norm(dim=1)
+    s = (b if scale is None else scale).transpose(0, 1).reshape(5, -1).norm(dim=1)
+    return (d / s).max().item()
+
+
+CASES = [
+    # (name, mesh kwargs, solver kwargs, state)
+    ("tgv_lgl_N3_roe", dict(nelem=(3, 3, 3), reorient_seed=1), dict(N=3, node_type=1, riemann=0), "tgv"),
+    ("tgv_lg_N1_hllc", dict(nelem=(3, 3, 3), reorient_seed=2), dict(N=1, riemann=1), "perturbed"),
+    ("pert_lg_N2_roe", dict(nelem=(3, 2, 5), reorient_seed=3), dict(N=2, riemann=0), "perturbed"),
+    ("pert_lg_N4_hllc", dict(nelem=(2, 3, 2), reorient_seed=4), dict(N=4, riemann=1), "perturbed"),
+    ("pert_lg_N5_roesmooth", dict(nelem=(2, 2, 3), reorient_seed=5), dict(N=5, riemann=2, mu=1 / 400.0), "perturbed"),
+    ("tgv_lg_N7_hllc", dict(nelem=(2, 2, 3), reorient_seed=6), dict(N=7, riemann=1), "tgv"),
+    ("pert_lgl_N6_hllc", dict(nelem=(2, 2, 2), reorient_seed=7), dict(N=6, node_type=1, riemann=1), "perturbed"),
+    ("curved_fs_lg_N4", dict(nelem=(3, 2, 2), lo=(-1,) * 3, hi=(1,) * 3, Ngeo=4, mapping="sine",
+                             periodic=(False,) * 3, reorient_seed=8),
+     dict(N=4, Ngeo=4, riemann=1, bc_exact=1), "perturbed_small"),
+    ("curved_mms_lg_N3", dict(nelem=(2, 3, 2), lo=(-1,) * 3, hi=(1,) * 3, Ngeo=3, mapping="sine",
+                              periodic=(False, True, False)),
+     dict(N=3, Ngeo=3, riemann=1, bc_exact=2, source=True), "manufactured"),
+]
+
+
+def _state(kind, mesh, N, nt):
+    x = mesh.node_coords(N, nt)
+    if kind == "tgv":
+        return wl.taylor_green(x)
+    if kind == "perturbed":
+        return wl.perturbed(x, seed=11)
+    if kind == "perturbed_small":
+        return wl.freestream(x) * (1 + 0.01 * np.sin(3 * x[:, :1]))
+    return wl.manufactured(x, 0.0)
+
+
+@pytest.mark.parametrize("name,mk,sk,state", CASES, ids=[c[0] for c in CASES])
+def test_rhs_parity_fp64(name, mk, sk, state):
+    mesh = wl.box_mesh(**mk)
+    sk = dict(sk, precision=0)
+    s = _solver(sk, mesh)
+    dg = _oracle(sk, mesh)
+    U0 = _state(state, mesh, sk["N"], sk.get("node_type", 0))
+    t = 0.1
+    Ut = s.rhs(torch.tensor(U0, device=DEV), t)
+    ref, parts = dg.rhs(torch.tensor(U0), t, parts=True)
+    scale = ref.abs() + (parts["vol"] / dg.geo.J.unsqueeze(1)).abs()
+    err = per_var_rel(Ut, ref, scale)
+    s.close()
+    assert err < 1e-12, err
+
+
+def test_freestream_curved_50_steps():
+    """C4a shape (reduced): the free stream stays exact on the curved mesh."""
+    N = 7
+    mesh = wl.box_mesh((3, 3, 3), lo=(-1,) * 3, hi=(1,) * 3, Ngeo=N, mapping="sine", periodic=(False,) * 3)
+    s = _solver(dict(N=N, Ngeo=N, riemann=1, bc_exact=1), mesh)
+    U0 = torch.tensor(wl.freestream(mesh.node_coords(N, 0)), device=DEV)
+    U = U0.clone()
+    s.run(U, 50, 1e-3)
+    err = (U - U0).abs().max().item()
+    s.close()
+    assert err < 1e-12, err
+
+
+def test_rk_steps_c1_config():
+    """C1: 4^3 periodic, N=3 LGL, Roe, 10 LSERK4(5) steps of dt = 1e-3."""
+    mesh = wl.box_mesh((4, 4, 4), Ngeo=1)
+    sk = dict(N=3, node_type=1, riemann=0)
+    s = _solver(sk, mesh)
+    dg = _oracle(sk, mesh)
+    U0 = wl.taylor_green(mesh.node_coords(3, 1))
+    U = torch.tensor(U0, device=DEV)
+    s.run(U, 10, 1e-3)
+    ref = dg.run(torch.tensor(U0), 10, 1e-3)
+    err = per_var_rel(U, ref)
+    s.close()
+    assert err < 1e-12, err
+
+
+def test_rk_steps_stages_and_reorientation():
+    """rk_step_stages stores the five stage inputs; reoriented frames, N=5."""
+    mesh = wl.box_mesh((3, 2, 2), Ngeo=1, reorient_seed=12)
+    sk = dict(N=5, riemann=1)
+    s = _solver(sk, mesh)
+    dg = _oracle(sk, mesh)
+    U0 = wl.perturbed(mesh.node_coords(5, 0), seed=4)
+    U = torch.tensor(U0, device=DEV)
+    dU = torch.zeros_like(U)
+    stages = torch.empty((5,) + U.shape, dtype=U.dtype, device=DEV)
+    s.step_stages(U, dU, 0.0, 2e-3, stages)
+    st_ref = []
+    Ur, dUr = dg.rk_step(torch.tensor(U0), torch.zeros_like(torch.tensor(U0)), 0.0, 2e-3, stages_out=st_ref)
+    assert per_var_rel(U, Ur) < 1e-12
+    assert per_var_rel(dU, dUr) < 1e-11
+    for k in range(5):
+        assert per_var_rel(stages[k], st_ref[k]) < 1e-12
+    s.close()
+
+
+def test_c2_full_size_rhs_and_invariants():
+    """C2 at full size (16^3, N=7 Gauss, HLLC): one RHS against the oracle, then
+    100 steps with conservation of mass, momentum and energy and decaying KE."""
+    N = 7
+    mesh = wl.box_mesh((16, 16, 16), Ngeo=1)
+    sk = dict(N=N, riemann=1)
+    s = _solver(sk, mesh)
+    U0 = wl.taylor_green(mesh.node_coords(N, 0))
+    U = torch.tensor(U0, device=DEV)
+    Ut = s.rhs(U, 0.0)
+    dg = _oracle(sk, mesh)
+    ref, parts = dg.rhs(torch.tensor(U0), 0.0, parts=True)
+    scale = ref.abs() + (parts["vol"] / dg.geo.J.unsqueeze(1)).abs()
+    assert per_var_rel(Ut, ref, scale) < 1e-12
+    r0 = s.reduce(U)
+    o_int = dg.integrals(torch.tensor(U0))
+    assert abs(r0["kinetic_energy"] - float(o_int[5])) < 1e-12 * abs(float(o_int[5]))
+    assert abs(r0["dt_max"] - dg.dt_max(torch.tensor(U0), 0.9)) < 1e-12 * r0["dt_max"]
+    dt = r0["dt_max"]
+    del dg, parts, ref
+    s.run(U, 100, dt)
+    r1 = s.reduce(U)
+    for key in ("mass", "mom_x", "mom_y", "mom_z", "energy"):
+        assert abs(r1[key] - r0[key]) < 1e-12 * max(1.0, abs(r0["energy"])), key
+    assert r1["kinetic_energy"] < r0["kinetic_energy"]
+    s.close()
+
+
+def test_reduce_matches_oracle():
+    mesh = wl.box_mesh((3, 3, 2), Ngeo=1, reorient_seed=3)
+    sk = dict(N=4, riemann=1)
+    s = _solver(sk, mesh)
+    dg = _oracle(sk, mesh)
+    U0 = wl.perturbed(mesh.node_coords(4, 0), seed=8)
+    U = torch.tensor(U0, device=DEV)
+    Ut = s.rhs(U)
+    r = s.reduce(U, Ut, cfl=0.5)
+    ints = dg.integrals(torch.tensor(U0))
+    for q, key in enumerate(["mass", "mom_x", "mom_y", "mom_z", "energy", "kinetic_energy"]):
+        assert abs(r[key] - float(ints[q])) < 1e-12 * max(1.0, abs(float(ints[q]))), key
+    Ut_ref = dg.rhs(torch.tensor(U0))
+    with torch.enable_grad():
+        Ux = torch.tensor(U0).requires_grad_(True)
+        (gk,) = torch.autograd.grad(dg.kinetic_energy(Ux), Ux)
+    dkedt = float((gk * Ut_ref).sum())
+    assert abs(r["dkedt"] - dkedt) < 1e-10 * max(1.0, abs(dkedt))
+    assert abs(r["dt_max"] - dg.dt_max(torch.tensor(U0), 0.5, 0.5)) < 1e-13 * r["dt_max"]
+    s.close()
+
+
+def test_run_host_matches_device_path():
+    mesh = wl.box_mesh((3, 3, 3), Ngeo=1)
+    sk = dict(N=3, riemann=1)
+    s = _solver(sk, mesh)
+    U0 = torch.tensor(wl.taylor_green(mesh.node_coords(3, 0)))
+    Uh = U0.clone().pin_memory()
+    from paper_1910_02858_gb300 import flexi as F
+
+    F.flexi_rk_run_host(s.ctx, Uh, 3, 0.0, 1e-3, torch.cuda.current_stream())
+    Ud = U0.to(DEV)
+    s.run(Ud, 3, 1e-3)
+    torch.cuda.synchronize()
+    assert torch.equal(Uh, Ud.cpu())
+    s.close()
+
+
+def test_nonphysical_state_reported():
+    from paper_1910_02858_gb300 import flexi as F
+
+    mesh = wl.box_mesh((2, 2, 2), Ngeo=1)
+    s = _solver(dict(N=2, riemann=1), mesh)
+    U0 = wl.taylor_green(mesh.node_coords(2, 0))
+    U0[3, 0] = -1.0  # negative density in one element (host-side injection)
+    U = torch.tensor(U0, device=DEV)
+    s.rhs(U)
+    r = s.reduce(torch.tensor(wl.taylor_green(mesh.node_coords(2, 0)), device=DEV), allow_nonphysical=True)
+    assert r["status"] == F.FLEXI_ENONPHYSICAL
+    assert s.query(F.Q_STATUS) == 0  # cleared by the report
+    s.close()
+
+
+def test_mesh_errors():
+    from paper_1910_02858_gb300 import flexi as F
+
+    mesh = wl.box_mesh((2, 2, 2), Ngeo=1)
+    conn = mesh.conn.copy()
+    conn[0, 1, 2] = (conn[0, 1, 2] + 1) % 8  # orientation not the inverse of the neighbour's
+    with pytest.raises(F.FlexiError) as ei:
+        _solver(dict(N=2), wl.BoxMesh(**{**mesh.__dict__, "conn": conn}))
+    assert ei.value.code == F.FLEXI_EMESH
+    coords = mesh.coords.copy()
+    coords[0] = coords[0][:, :, ::-1]  # mirrored element: J < 0
+    with pytest.raises(F.FlexiError) as ei:
+        _solver(dict(N=2), wl.BoxMesh(**{**mesh.__dict__, "coords": coords}))
+    assert ei.value.code == F.FLEXI_EMESH
+    with pytest.raises(F.FlexiError) as ei:
+        _solver(dict(N=8), mesh)
+    assert ei.value.code == F.FLEXI_EUNSUPPORTED
+
+
+def test_kernel_timing_hooks():
+    from paper_1910_02858_gb300 import flexi as F
+
+    mesh = wl.box_mesh((4, 4, 4), Ngeo=1)
+    s = _solver(dict(N=3), mesh)
+    U = torch.tensor(wl.taylor_green(mesh.node_coords(3, 0)), device=DEV)
+    F.flexi_profile(s.ctx, True)
+    s.run(U, 2, 1e-3)
+    t = F.flexi_kernel_times(s.ctx)
+    assert t["lift_vol"][1] == 10 and t["face"][1] == 10 and t["surf_rk"][1] == 10 and t["prolong"][1] == 2
+    assert all(v[0] >= 0 for v in t.values())
+    s.close()
