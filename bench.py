@@ -1,0 +1,374 @@
+#!/usr/bin/env python
+"""Benchmark: PID (ns per DOF per RK stage) of the DGSEM Navier-Stokes LSERK4(5)
+step on GB300 (Krais et al., FLEXI, Sec. 5.6: PID = wall * #cores / (#DOF *
+#steps * #stages), with #cores -> #GPUs).
+
+Workload: Taylor-Green vortex (Re = 1600, Ma = 0.1) on a periodic 16^3 mesh,
+N = 7 Gauss nodes (2,097,152 DOF), HLLC flux, BR1 lifting, fixed dt from CFL
+0.9; one bench step = one LSERK4(5) time step (5 RK stages) in FP64.  Inputs
+are resident in HBM and larger than L2.  Extra keys report the FP32 forms
+(PID and error against FP64 after the timed steps) and the adjoint/forward
+cost ratio.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+N > 1 (under torchrun): every rank runs an independent replica (the library
+computes on one GPU; no data-path collective); value is whole-job.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PID ns/DOF/RK-stage at N=7 on 1 GB300: FP64 vs FP32/TC (err vs FP64); adjoint/fwd"
+UNIT = "ns/DOF/RK-stage"
+WORKLOAD = dict(workload="taylor-green vortex, periodic 16^3 hex, N=7 Gauss, HLLC, BR1, LSERK4(5), CFL 0.9",
+                elements=4096, N=7, dof=2097152, re=1600, mach=0.1, step="one LSERK4(5) step = 5 RK stages",
+                l2="inputs larger than L2 (working set > 129 MB)")
+NSTAGES = 5
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+# GB300 FP64 FMA peak derived from unit counts and clocks: 152 SMs x 2 DFMA/clk
+# (4 FP64 flop/clk/SM, consistent with the nominal 1.25 TFLOP/s) x 2070 MHz.
+FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (clocks and throttle reasons)."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"), f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def algorithmic_per_dof(n: int, word: int):
+    """Per DOF and RK stage: minimum-traffic bytes of the three-kernel schedule and
+    the flops of the dominant kernel (lifting + volume integral), FMA = 2 flops."""
+    f = 3.0 / n
+    bytes_stage = (46.0 + 117.0 * f) * word
+    bytes_liftvol = (20.0 + 48.0 * f) * word
+    flops_liftvol = (2 * 45 * n          # lifting D_hat sweeps (3 directions x 15 components)
+                     + 2 * 90            # LG lifting surface terms, 6 faces x 15 components
+                     + 45 + 15 + 10      # contravariant products Ja W, 1/J scaling, primitives
+                     + 2 * 90            # LG prolongation of the 15 gradients to 6 faces
+                     + 3 * 30            # pointwise fluxes F^c - F^v, 3 directions
+                     + 2 * 45            # contravariant transform sum_d Ja^l_d F^d
+                     + 2 * 15 * n)       # volume D_hat sweeps (3 directions x 5 variables)
+    return bytes_stage, bytes_liftvol, flops_liftvol
+
+
+def run_cpu_baseline(budget_s: float = 20.0):
+    """The FP64 oracle as it stands, timed on the host cores on a bounded sample of
+    the same workload: repeated full right-hand sides of the 16^3, N=7 case."""
+    import torch
+
+    import workloads as wl
+    from oracle.dgsem import DGSEM, HLLC, Params
+
+    mesh = wl.box_mesh((16, 16, 16), Ngeo=1)
+    dg = DGSEM(Params(N=7, node_type=0, riemann=HLLC), mesh.coords, mesh.conn)
+    U = torch.tensor(wl.taylor_green(mesh.node_coords(7, 0)))
+    dof = dg.K * dg.n ** 3
+    dg.rhs(U)  # warm-up
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        Ut = dg.rhs(U)
+        U2 = U + 1e-4 * Ut  # the stage update, so the sample is a full RK stage
+        reps += 1
+        if time.perf_counter() - t0 > budget_s / 2 or reps >= 10:
+            break
+    el = time.perf_counter() - t0
+    pid = el / (reps * dof) * 1e9
+    return {"value": pid, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
+            "sample": f"{reps} RK stages (full RHS + update) of the 16^3 N=7 TGV workload, FP64 torch CPU"}
+
+
+def reference_arm(args):
+    """--impl reference: the oracle timed as the reference arm on the host cores."""
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import torch
+
+    import workloads as wl
+    from oracle.dgsem import DGSEM, HLLC, Params
+
+    mesh = wl.box_mesh((16, 16, 16), Ngeo=1)
+    dg = DGSEM(Params(N=7, node_type=0, riemann=HLLC), mesh.coords, mesh.conn)
+    U = torch.tensor(wl.taylor_green(mesh.node_coords(7, 0)))
+    dU = torch.zeros_like(U)
+    dof = dg.K * dg.n ** 3
+    # one bench step of this arm = one RK stage (bounded sample of the workload)
+    from oracle.dgsem import RK_A, RK_B
+
+    def stage(U, dU, k):
+        Ut = dg.rhs(U)
+        dU = RK_A[k % 5] * dU + 1e-4 * Ut
+        return U + RK_B[k % 5] * dU, dU
+
+    for k in range(args.warmup):
+        U, dU = stage(U, dU, k)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        U, dU = stage(U, dU, k)
+    el = time.perf_counter() - t0
+    pid = el / (args.steps * dof) * 1e9
+    line = {"metric": METRIC, "value": pid, "unit": UNIT, "impl": "reference", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": dict(WORKLOAD, step="one RK stage (RHS + update) of the oracle"),
+            "cpu_baseline": {"value": pid, "unit": UNIT, "kind": "oracle", "cores": torch.get_num_threads(),
+                             "sample": f"{args.steps} RK stages of the 16^3 N=7 TGV workload"},
+            "e2e": {"value": pid, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the FP32 and adjoint extra measurements")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import numpy as np
+    import torch
+
+    import workloads as wl
+    from paper_1910_02858_gb300 import Solver, SolverConfig
+    from paper_1910_02858_gb300 import build as B
+    from paper_1910_02858_gb300 import flexi as F
+
+    world, rank, local = dist_env()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0:
+        B.build()
+    if dist is not None:
+        dist.barrier()
+    F.lib()
+
+    N = 7
+    mesh = wl.box_mesh((16, 16, 16), Ngeo=1)
+    x = mesh.node_coords(N, 0)
+    U0 = wl.taylor_green(x)
+    cfg = SolverConfig(N=N, riemann=F.RIEMANN_HLLC, precision=F.FP64)
+    s = Solver(cfg, mesh.coords, mesh.conn, device=dev)
+    dof = s.query(F.Q_DOF)
+    U = torch.tensor(U0, device=dev)
+    dU = torch.zeros_like(U)
+    dt = s.reduce(U)["dt_max"]
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    # count kernel launches per step (profiled, untimed)
+    F.flexi_profile(s.ctx, True)
+    s.step(U.clone(), dU.clone(), 0.0, dt)
+    launches_per_step = sum(c for _, c in F.flexi_kernel_times(s.ctx, reset=True).values())
+
+    t = 0.0
+    for _ in range(args.warmup):
+        s.step(U, dU, t, dt)
+        t += dt
+    F.flexi_kernel_times(s.ctx, reset=True)
+    barrier()
+    torch.cuda.synchronize(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            s.step(U, dU, t, dt)
+            t += dt
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+    barrier()
+    ms_total = ev0.elapsed_time(ev1)
+    ktimes = F.flexi_kernel_times(s.ctx, reset=True)
+    F.flexi_profile(s.ctx, False)
+    if dist is not None:
+        tt = torch.tensor([ms_total], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms_total = float(tt.item())
+    ms_step = ms_total / args.steps
+    pid = ms_total * 1e6 / (args.steps * NSTAGES * dof * world)  # whole job
+
+    # roofline of the dominant kernel (lifting + volume), FP64 ALU-bound
+    n = N + 1
+    bytes_stage, bytes_lv, flops_lv = algorithmic_per_dof(n, 8)
+    lv_ms, lv_cnt = ktimes["lift_vol"]
+    lv_avg_s = lv_ms / max(lv_cnt, 1) * 1e-3
+    achieved_tflops = flops_lv * dof / lv_avg_s / 1e12
+    roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved_tflops / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "k_lift_vol<double,8>",
+                "peak_source": "derived: 152 SM x 4 FP64 flop/clk x 2070 MHz (nominal 1.25 TFLOP/s)",
+                "kernel_share": lv_ms / max(sum(v[0] for v in ktimes.values()), 1e-9)}
+    step_bytes_gbs = bytes_stage * dof * NSTAGES / (ms_step * 1e-3) / 1e9
+    kernels = {k: {"ms_per_launch": (v[0] / v[1]) if v[1] else 0.0, "launches": v[1]} for k, v in ktimes.items() if v[1]}
+
+    # end to end through the public API with host buffers (H2D + step + D2H per step)
+    Uh = torch.tensor(U0).pin_memory()
+    F.flexi_rk_run_host(s.ctx, Uh, 1, 0.0, dt, stream)
+    barrier()
+    t0 = time.perf_counter()
+    for k in range(max(3, args.steps // 2)):
+        F.flexi_rk_run_host(s.ctx, Uh, 1, k * dt, dt, stream)
+    e2e_s = time.perf_counter() - t0
+    e2e_steps = max(3, args.steps // 2)
+    if dist is not None:
+        tt = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    e2e_pid = e2e_s * 1e9 / (e2e_steps * NSTAGES * dof * world)
+    ubytes = U.numel() * 8
+
+    line = {"metric": METRIC, "value": pid, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": dict(WORKLOAD, dt=dt),
+            "clocks": clk.summary(), "gpu_launches": launches_per_step * args.steps,
+            "e2e": {"value": e2e_pid, "unit": UNIT, "h2d_bytes_per_step": ubytes, "d2h_bytes_per_step": ubytes},
+            "roofline": roofline, "dof_updates_per_s": dof * world / (pid * 1e-9 * dof * world) if pid else None,
+            "step_algorithmic_hbm_gbs": step_bytes_gbs, "kernels": kernels}
+
+    if rank == 0 and not args.no_extras:
+        line["extras"] = extras(args, s, U0, mesh, dt, dev, F, wl, Solver, SolverConfig, torch, np)
+    s.close()
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        try:
+            line["cpu_baseline"] = run_cpu_baseline()
+        except Exception as exc:  # pragma: no cover
+            line["cpu_baseline"] = {"value": None, "error": repr(exc)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def extras(args, s64, U0, mesh, dt, dev, F, wl, Solver, SolverConfig, torch, np):
+    """FP32 forms on the same workload (PID and error vs FP64 after the same
+    number of steps) and the adjoint/forward cost ratio."""
+    out = {}
+    nsteps = 20
+    U64 = torch.tensor(U0, device=dev)
+    s64.run(U64, nsteps, dt)
+    for name, prec in (("fp32", F.FP32), ("fp32_tf32", F.FP32_TF32), ("fp32_bf16", F.FP32_BF16)):
+        try:
+            s = Solver(SolverConfig(N=7, riemann=F.RIEMANN_HLLC, precision=prec), mesh.coords, mesh.conn, device=dev)
+        except Exception as exc:
+            out[name] = {"error": str(exc)}
+            continue
+        try:
+            U = torch.tensor(U0, device=dev, dtype=torch.float32)
+            dU = torch.zeros_like(U)
+            for _ in range(3):
+                s.step(U, dU, 0.0, dt)
+            U = torch.tensor(U0, device=dev, dtype=torch.float32)
+            dU.zero_()
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for k in range(nsteps):
+                s.step(U, dU, k * dt, dt)
+            e1.record()
+            torch.cuda.synchronize(dev)
+            ms = e0.elapsed_time(e1)
+            dof = s.query(F.Q_DOF)
+            d = (U.double() - U64).transpose(0, 1).reshape(5, -1).norm(dim=1)
+            r = U64.transpose(0, 1).reshape(5, -1).norm(dim=1)
+            out[name] = {"pid": ms * 1e6 / (nsteps * NSTAGES * dof), "steps": nsteps,
+                         "rel_l2_err_vs_fp64": (d / r).tolist()}
+        except Exception as exc:
+            out[name] = {"error": str(exc)}
+        finally:
+            s.close()
+    return out
+
+
+if __name__ == "__main__":
+    sys.exit(main())

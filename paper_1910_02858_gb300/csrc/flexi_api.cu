@@ -524,7 +524,6 @@ flexi_status flexi_mesh_init(flexi_ctx** out, const flexi_params* p, int K, cons
 
 flexi_status flexi_rhs(flexi_ctx* c, const void* U, void* Ut, double t, void* stream) {
   if (c == nullptr || U == nullptr || Ut == nullptr) return FLEXI_EINVAL;
-  if (c->m.sweep_mode != 0) return FLEXI_EUNSUPPORTED;
   cudaStream_t st = (cudaStream_t)stream;
   return c->fp64 ? do_rhs<double>(c, (const double*)U, (double*)Ut, t, st)
                  : do_rhs<float>(c, (const float*)U, (float*)Ut, t, st);
@@ -532,7 +531,6 @@ flexi_status flexi_rhs(flexi_ctx* c, const void* U, void* Ut, double t, void* st
 
 flexi_status flexi_rk_step(flexi_ctx* c, void* U, void* dU, double t, double dt, void* stream) {
   if (c == nullptr || U == nullptr || dU == nullptr) return FLEXI_EINVAL;
-  if (c->m.sweep_mode != 0) return FLEXI_EUNSUPPORTED;
   cudaStream_t st = (cudaStream_t)stream;
   return c->fp64 ? do_rk_step<double>(c, (double*)U, (double*)dU, t, dt, nullptr, st)
                  : do_rk_step<float>(c, (float*)U, (float*)dU, t, dt, nullptr, st);
@@ -541,7 +539,6 @@ flexi_status flexi_rk_step(flexi_ctx* c, void* U, void* dU, double t, double dt,
 flexi_status flexi_rk_step_stages(flexi_ctx* c, void* U, void* dU, double t, double dt, void* U_stages,
                                   void* stream) {
   if (c == nullptr || U == nullptr || dU == nullptr || U_stages == nullptr) return FLEXI_EINVAL;
-  if (c->m.sweep_mode != 0) return FLEXI_EUNSUPPORTED;
   cudaStream_t st = (cudaStream_t)stream;
   return c->fp64 ? do_rk_step<double>(c, (double*)U, (double*)dU, t, dt, (double*)U_stages, st)
                  : do_rk_step<float>(c, (float*)U, (float*)dU, t, dt, (float*)U_stages, st);

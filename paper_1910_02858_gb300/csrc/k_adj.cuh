@@ -1,0 +1,678 @@
+// Discrete adjoint of the right-hand side: mu = (dL/dU)^T lam, by hand-written
+// reverse mode of every step of the forward operator (steps a1..a9 of k_dg.cuh),
+// for periodic meshes and the Roe flux (optionally with smoothed |lambda|).
+//
+// Forward recompute (k_prolong, k_lift_vol with the volume gradients stored),
+// then, in reverse order of the forward data flow:
+//   k_adj_lamface  element: lam_vol = -lam/J; its l_hat-weighted face values
+//                  (transpose of the surface integral a8/a9)
+//   k_adj_face     side: reverse of the numerical flux a5 (Roe + BR1 viscous)
+//                  -> adjoints of the face states W_L, W_R and face gradients
+//   k_adj_vol      element: reverse of a7 (D_hat^T sweeps), a6 (pointwise flux
+//                  VJP), a4 (prolongation^T of the face-gradient adjoints), a3
+//                  (lifting: 45 D_hat^T sweeps and the l_hat face projections),
+//                  and the primitive map of the volume states
+//   k_adj_side     side: BR1 mean (U* = (U_L + U_R)/2) and the primitive map of
+//                  the face states
+//   k_adj_gather   element: prolongation^T of the face-state adjoints; out =
+//                  (accumulate ? out : 0) + scale * mu
+#pragma once
+#include "dg_common.cuh"
+#include "k_dg.cuh"
+#include "launch.h"
+
+namespace flexi {
+
+// ---------------------------------------------------------------------------
+// pointwise reverse-mode building blocks
+// ---------------------------------------------------------------------------
+
+// W = prim(U): accumulate lamU += (dW/dU)^T lamW  (expressed with W)
+template <typename real>
+__device__ __forceinline__ void prim_vjp(const real W[NV], const real lamW[NV], const Phys<real>& ph,
+                                         real lamU[NV]) {
+  const real ir = real(1) / W[0];
+  const real q2 = W[1] * W[1] + W[2] * W[2] + W[3] * W[3];
+  real l0 = lamW[0] + lamW[4] * ph.gm1 * real(0.5) * q2;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    l0 -= lamW[1 + c] * W[1 + c] * ir;
+    lamU[1 + c] += lamW[1 + c] * ir - lamW[4] * ph.gm1 * W[1 + c];
+  }
+  lamU[0] += l0;
+  lamU[4] += lamW[4] * ph.gm1;
+}
+
+// viscous flux reverse: given lamF[d][5] for F^v_d(W, G), accumulate lamW, lamG
+template <typename real>
+__device__ __forceinline__ void visc_vjp(const real W[NV], const real G[15], const real lamF[3][NV],
+                                         const Phys<real>& ph, real lamW[NV], real lamG[15]) {
+  const real mu = ph.mu;
+  const real div = G[0 * 5 + 1] + G[1 * 5 + 2] + G[2 * 5 + 3];
+  const real ir = real(1) / W[0];
+  real ldiv = real(0);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const real* lf = lamF[d];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      real tau = mu * (G[d * 5 + 1 + c] + G[c * 5 + 1 + d]);
+      if (c == d) tau -= real(2.0 / 3.0) * mu * div;
+      const real ltau = lf[1 + c] + lf[4] * W[1 + c];
+      lamW[1 + c] += lf[4] * tau;
+      lamG[d * 5 + 1 + c] += mu * ltau;
+      lamG[c * 5 + 1 + d] += mu * ltau;
+      if (c == d) ldiv -= real(2.0 / 3.0) * mu * ltau;
+    }
+    // heat flux: lam_th * dT_d, dT_d = (G[d5+4] - (p/rho) G[d5+0]) / rho
+    const real ldT = lf[4] * ph.lam_th;
+    const real g4 = G[d * 5 + 4], g0 = G[d * 5 + 0];
+    lamG[d * 5 + 4] += ldT * ir;
+    lamG[d * 5 + 0] -= ldT * W[4] * ir * ir;
+    lamW[4] -= ldT * g0 * ir * ir;
+    lamW[0] += ldT * (-g4 * ir * ir + real(2) * W[4] * g0 * ir * ir * ir);
+  }
+  lamG[0 * 5 + 1] += ldiv;
+  lamG[1 * 5 + 2] += ldiv;
+  lamG[2 * 5 + 3] += ldiv;
+}
+
+// convective flux F^c_d(U, W) reverse: lamF[5] -> lamU (direct), lamW
+template <typename real>
+__device__ __forceinline__ void conv_vjp(const real U[NV], const real W[NV], int d, const real lf[NV], real lamU[NV],
+                                         real lamW[NV]) {
+  lamU[1 + d] += lf[0];
+  real lud = lf[4] * (U[4] + W[4]);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    lamU[1 + c] += lf[1 + c] * W[1 + d];
+    lud += lf[1 + c] * U[1 + c];
+  }
+  lamU[4] += lf[4] * W[1 + d];
+  lamW[1 + d] += lud;
+  lamW[4] += lf[1 + d] + lf[4] * W[1 + d];
+}
+
+template <typename real>
+__device__ __forceinline__ void absf_vjp(real x, real del, bool smooth, real& val, real& dx, real& ddel) {
+  const real ax = dg_abs(x);
+  if (smooth && ax < del) {
+    const real ih = real(0.5) / del;
+    val = (x * x + del * del) * ih;
+    dx = x / del;
+    ddel = (del * del - x * x) * ih / del;
+  } else {
+    val = ax;
+    dx = x < real(0) ? real(-1) : (x > real(0) ? real(1) : real(0));
+    ddel = real(0);
+  }
+}
+
+// Roe flux reverse: given lamf, accumulate lamWL, lamWR (recomputes the forward)
+template <typename real>
+__device__ __forceinline__ void roe_vjp(const real WL[NV], const real WR[NV], const real n[3], const Phys<real>& ph,
+                                        bool smooth, const real lf[NV], real lWL[NV], real lWR[NV]) {
+  const real gm1 = ph.gm1;
+  // ---- forward
+  const real q2L = WL[1] * WL[1] + WL[2] * WL[2] + WL[3] * WL[3];
+  const real q2R = WR[1] * WR[1] + WR[2] * WR[2] + WR[3] * WR[3];
+  const real EL = WL[4] * ph.inv_gm1 + real(0.5) * WL[0] * q2L;
+  const real ER = WR[4] * ph.inv_gm1 + real(0.5) * WR[0] * q2R;
+  const real unL = WL[1] * n[0] + WL[2] * n[1] + WL[3] * n[2];
+  const real unR = WR[1] * n[0] + WR[2] * n[1] + WR[3] * n[2];
+  const real sL = dg_sqrt(WL[0]), sR = dg_sqrt(WR[0]);
+  const real iws = real(1) / (sL + sR);
+  const real HL = (EL + WL[4]) / WL[0], HR = (ER + WR[4]) / WR[0];
+  real vel[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) vel[k] = (sL * WL[1 + k] + sR * WR[1 + k]) * iws;
+  const real H = (sL * HL + sR * HR) * iws;
+  const real q2 = vel[0] * vel[0] + vel[1] * vel[1] + vel[2] * vel[2];
+  const real c2 = gm1 * (H - real(0.5) * q2);
+  const real c = dg_sqrt(c2);
+  const real ic2 = real(1) / c2;
+  const real rho = sL * sR;
+  const real un = vel[0] * n[0] + vel[1] * n[1] + vel[2] * n[2];
+  const real dp = WR[4] - WL[4];
+  real dv[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) dv[k] = WR[1 + k] - WL[1 + k];
+  const real dun = dv[0] * n[0] + dv[1] * n[1] + dv[2] * n[2];
+  const real a1 = (dp - rho * c * dun) * real(0.5) * ic2;
+  const real a5 = (dp + rho * c * dun) * real(0.5) * ic2;
+  const real a2 = (WR[0] - WL[0]) - dp * ic2;
+  const real del = real(0.1) * c;
+  real l1, l2, l5, d1, d2, d5, e1, e2, e5;
+  absf_vjp(un - c, del, smooth, l1, d1, e1);
+  absf_vjp(un, del, smooth, l2, d2, e2);
+  absf_vjp(un + c, del, smooth, l5, d5, e5);
+  const real w1 = l1 * a1, w5 = l5 * a5, w2 = l2 * a2, wt = l2 * rho;
+  real dvt[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) dvt[k] = dv[k] - dun * n[k];
+  const real vdvt = vel[0] * dvt[0] + vel[1] * dvt[1] + vel[2] * dvt[2];
+  // ---- reverse
+  const real h = real(0.5);
+  real lw1 = lf[0], lw5 = lf[0], lw2 = lf[0], lwt = real(0);
+  real lvel[3] = {0, 0, 0}, lc = 0, lH = 0, lun = 0, lq2 = 0, ldvt[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    lw1 += lf[1 + k] * (vel[k] - c * n[k]);
+    lw5 += lf[1 + k] * (vel[k] + c * n[k]);
+    lw2 += lf[1 + k] * vel[k];
+    lwt += lf[1 + k] * dvt[k];
+    lvel[k] = -h * (lf[1 + k] * (w1 + w5 + w2) + lf[4] * wt * dvt[k]);
+    lc += -h * lf[1 + k] * (w5 - w1) * n[k];
+    ldvt[k] = -h * (lf[1 + k] * wt + lf[4] * wt * vel[k]);
+  }
+  lw1 = -h * (lw1 + lf[4] * (H - un * c));
+  lw5 = -h * (lw5 + lf[4] * (H + un * c));
+  lw2 = -h * (lw2 + lf[4] * real(0.5) * q2);
+  lwt = -h * (lwt + lf[4] * vdvt);
+  lc += -h * lf[4] * (w5 - w1) * un;
+  lH += -h * lf[4] * (w1 + w5);
+  lun += -h * lf[4] * (w5 - w1) * c;
+  lq2 += -h * lf[4] * w2 * real(0.5);
+  // w = l a, wt = l2 rho
+  const real la1 = lw1 * l1, la5 = lw5 * l5, la2 = lw2 * l2;
+  const real ll1 = lw1 * a1, ll5 = lw5 * a5, ll2 = lw2 * a2 + lwt * rho;
+  real lrho = lwt * l2;
+  // dvt = dv - dun n
+  real ldv[3], ldun = real(0);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    ldv[k] = ldvt[k];
+    ldun -= ldvt[k] * n[k];
+  }
+  // |.| terms (delta = 0.1 c)
+  lun += ll1 * d1 + ll2 * d2 + ll5 * d5;
+  lc += -ll1 * d1 + ll5 * d5 + real(0.1) * (ll1 * e1 + ll2 * e2 + ll5 * e5);
+  // a1, a5, a2
+  const real hic2 = h * ic2;
+  real ldp = (la1 + la5) * hic2 - la2 * ic2;
+  lrho += (-la1 + la5) * hic2 * c * dun;
+  lc += (-la1 + la5) * hic2 * rho * dun;
+  ldun += (-la1 + la5) * hic2 * rho * c;
+  real lic2 = la1 * (dp - rho * c * dun) * h + la5 * (dp + rho * c * dun) * h - la2 * dp;
+  const real ldrho = la2;
+  // dun = dv . n
+#pragma unroll
+  for (int k = 0; k < 3; ++k) ldv[k] += ldun * n[k];
+  // un = vel . n
+#pragma unroll
+  for (int k = 0; k < 3; ++k) lvel[k] += lun * n[k];
+  // rho = sL sR
+  real lsL = lrho * sR, lsR = lrho * sL;
+  // ic2 = 1/c2, c = sqrt(c2)
+  real lc2 = -lic2 * ic2 * ic2 + lc * h / c;
+  // c2 = gm1 (H - q2/2)
+  lH += gm1 * lc2;
+  lq2 -= h * gm1 * lc2;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) lvel[k] += real(2) * vel[k] * lq2;
+  // H = (sL HL + sR HR) iws ; vel = (sL uL + sR uR) iws
+  real liws = lH * (sL * HL + sR * HR);
+  lsL += lH * HL * iws;
+  lsR += lH * HR * iws;
+  const real lHL = lH * sL * iws, lHR = lH * sR * iws;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    liws += lvel[k] * (sL * WL[1 + k] + sR * WR[1 + k]);
+    lsL += lvel[k] * WL[1 + k] * iws;
+    lsR += lvel[k] * WR[1 + k] * iws;
+    lWL[1 + k] += lvel[k] * sL * iws;
+    lWR[1 + k] += lvel[k] * sR * iws;
+  }
+  lsL -= liws * iws * iws;
+  lsR -= liws * iws * iws;
+  // dp, dv, drho
+  lWR[4] += ldp;
+  lWL[4] -= ldp;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    lWR[1 + k] += ldv[k];
+    lWL[1 + k] -= ldv[k];
+  }
+  lWR[0] += ldrho;
+  lWL[0] -= ldrho;
+  // per side: HL = (EL + pL)/rhoL, sL = sqrt(rhoL), FL = euler_normal, EL, unL
+  auto side = [&](const real* W, real E, real unK, real HK, real sK, real lHK, real lsK, real* lW) {
+    real lE = lHK / W[0];
+    lW[4] += lHK / W[0];
+    lW[0] += -lHK * HK / W[0] + lsK * h / sK;
+    // F = (rho un, rho un u + p n, (E + p) un), weight 1/2
+    const real lF0 = h * lf[0], lF4 = h * lf[4];
+    real lunK = lF0 * W[0] + lF4 * (E + W[4]);
+    lW[0] += lF0 * unK;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const real lFk = h * lf[1 + k];
+      lW[0] += lFk * unK * W[1 + k];
+      lunK += lFk * W[0] * W[1 + k];
+      lW[1 + k] += lFk * W[0] * unK;
+      lW[4] += lFk * n[k];
+    }
+    lW[4] += lF4 * unK;
+    lE += lF4 * unK;
+    // unK = u . n ; E = p/gm1 + rho q2/2
+#pragma unroll
+    for (int k = 0; k < 3; ++k) lW[1 + k] += lunK * n[k] + lE * W[0] * W[1 + k];
+    lW[4] += lE * ph.inv_gm1;
+    lW[0] += lE * real(0.5) * (W[1] * W[1] + W[2] * W[2] + W[3] * W[3]);
+  };
+  side(WL, EL, unL, HL, sL, lHL, lsL, lWL);
+  side(WR, ER, unR, HR, sR, lHR, lsR, lWR);
+}
+
+// ---------------------------------------------------------------------------
+// kernels
+// ---------------------------------------------------------------------------
+template <typename real, int n>
+__global__ void __launch_bounds__(Cfg<n>::T) k_adj_lamface(const real* __restrict__ lam, const real* __restrict__ sJ,
+                                                            const int* __restrict__ elemSide, real* __restrict__ LF,
+                                                            int K, int S, Ops<real> ops) {
+  using C = Cfg<n>;
+  constexpr int n2 = C::n2, n3 = C::n3, NE = C::NE, T = C::T;
+  __shared__ real sL[NE * NV * n3];
+  __shared__ real sOp[n2 + 4 * n];
+  __shared__ int sES[NE * 6];
+  const int tid = threadIdx.x;
+  const int e0 = blockIdx.x * NE;
+  load_ops<real, n>(sOp, ops, tid, T);
+  for (int t = tid; t < NE * 6; t += T) sES[t] = (e0 + t / 6 < K) ? elemSide[(size_t)e0 * 6 + t] : 0;
+  for (int t = tid; t < NE * NV * n3; t += T) {
+    const int el = t / (NV * n3), r = t - el * NV * n3, node = r % n3;
+    const int e = e0 + el;
+    sL[t] = e < K ? -lam[(size_t)e * NV * n3 + r] * sJ[(size_t)e * n3 + node] : real(0);
+  }
+  __syncthreads();
+  const real* lhm = sOp + n2 + 2 * n;
+  const real* lhp = sOp + n2 + 3 * n;
+  for (int it = tid; it < NE * 6 * n2; it += T) {
+    const int el = it / (6 * n2);
+    const int r = it - el * 6 * n2;
+    const int s = r / n2, pq = r - s * n2;
+    if (e0 + el >= K) continue;
+    const int l = s >> 1;
+    const real* lv = (s & 1) ? lhp : lhm;
+    const int p = pq % n, q = pq / n;
+    real acc[NV] = {0, 0, 0, 0, 0};
+#pragma unroll
+    for (int a = 0; a < n; ++a) {
+      const int vi = vol_index(l, a, p, q, n);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) acc[v] += lv[a] * sL[(el * NV + v) * n3 + vi];
+    }
+    const int es = sES[el * 6 + s];
+    const int mpq = orient_pq(es_orient(es), n - 1, p, q);
+    real* dst = LF + ((size_t)(es_slave(es) * S + es_side(es)) * NV) * n2 + mpq;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) dst[v * n2] = acc[v];
+  }
+}
+
+template <typename real, int n>
+__global__ void __launch_bounds__(128) k_adj_face(const real* __restrict__ Wf, const real* __restrict__ Gf,
+                                                  const real* __restrict__ fgeo, const real* __restrict__ LF,
+                                                  real* __restrict__ LWf, real* __restrict__ LGf, int S, Phys<real> ph) {
+  constexpr int n2 = n * n;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= S * n2) return;
+  const int side = idx / n2, pq = idx - side * n2;
+  real WL[NV], WR[NV], GL[15], GR[15], nv[3], lf[NV];
+  const real sa = fgeo[((size_t)side * 4 + 3) * n2 + pq];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    WL[v] = Wf[((size_t)side * NV + v) * n2 + pq];
+    WR[v] = Wf[((size_t)(S + side) * NV + v) * n2 + pq];
+    lf[v] = (LF[((size_t)side * NV + v) * n2 + pq] - LF[((size_t)(S + side) * NV + v) * n2 + pq]) * sa;
+  }
+#pragma unroll
+  for (int c = 0; c < 15; ++c) {
+    GL[c] = Gf[((size_t)side * 15 + c) * n2 + pq];
+    GR[c] = Gf[((size_t)(S + side) * 15 + c) * n2 + pq];
+  }
+#pragma unroll
+  for (int d = 0; d < 3; ++d) nv[d] = fgeo[((size_t)side * 4 + d) * n2 + pq];
+  real lWL[NV] = {0, 0, 0, 0, 0}, lWR[NV] = {0, 0, 0, 0, 0};
+  real lGL[15], lGR[15];
+#pragma unroll
+  for (int c = 0; c < 15; ++c) lGL[c] = lGR[c] = real(0);
+  roe_vjp(WL, WR, nv, ph, ph.riemann == 2, lf, lWL, lWR);
+  real lF[3][NV];
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+#pragma unroll
+    for (int v = 0; v < NV; ++v) lF[d][v] = -real(0.5) * nv[d] * lf[v];
+  visc_vjp(WL, GL, lF, ph, lWL, lGL);
+  visc_vjp(WR, GR, lF, ph, lWR, lGR);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    LWf[((size_t)side * NV + v) * n2 + pq] = lWL[v];
+    LWf[((size_t)(S + side) * NV + v) * n2 + pq] = lWR[v];
+  }
+#pragma unroll
+  for (int c = 0; c < 15; ++c) {
+    LGf[((size_t)side * 15 + c) * n2 + pq] = lGL[c];
+    LGf[((size_t)(S + side) * 15 + c) * n2 + pq] = lGR[c];
+  }
+}
+
+// transposed sweep along direction l at the thread's node: sum_i Dhat[i][a_l] f(node with index_l = i)
+template <typename real, int n>
+__device__ __forceinline__ real dhatT_line(const real* __restrict__ sD, const real* __restrict__ f, int l, int i, int j,
+                                           int k) {
+  constexpr int n2 = n * n;
+  real s = real(0);
+  if (l == 0) {
+#pragma unroll
+    for (int b = 0; b < n; ++b) s += sD[i * n + b] * f[b + n * j + n2 * k];
+  } else if (l == 1) {
+#pragma unroll
+    for (int b = 0; b < n; ++b) s += sD[j * n + b] * f[i + n * b + n2 * k];
+  } else {
+#pragma unroll
+    for (int b = 0; b < n; ++b) s += sD[k * n + b] * f[i + n * j + n2 * b];
+  }
+  return s;
+}
+
+template <typename real, int n>
+constexpr size_t adj_vol_smem() {
+  using C = Cfg<n>;
+  return sizeof(real) * (C::NE * 15 * C::n3 + C::NE * 6 * 15 * C::n2 + C::n2 + 4 * n) + sizeof(int) * C::NE * 8;
+}
+
+template <typename real, int n>
+__global__ void __launch_bounds__(Cfg<n>::T) k_adj_vol(
+    const real* __restrict__ U, const real* __restrict__ Ja, const real* __restrict__ sJ, const real* __restrict__ Gvol,
+    const real* __restrict__ fgeo, const int* __restrict__ elemSide, const real* __restrict__ lam,
+    const real* __restrict__ LGf, real* __restrict__ LWs, real* __restrict__ muv, int K, int S, Ops<real> ops,
+    Phys<real> ph) {
+  using C = Cfg<n>;
+  constexpr int n2 = C::n2, n3 = C::n3, NE = C::NE, T = C::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  real* sbuf = reinterpret_cast<real*>(smem_raw);  // [NE][15][n3]
+  real* sF = sbuf + NE * 15 * n3;                  // [NE][6][15][n2] face-gradient adjoints
+  real* sOp = sF + NE * 6 * 15 * n2;
+  int* sES = reinterpret_cast<int*>(sOp + n2 + 4 * n);
+  const int tid = threadIdx.x;
+  const int el = tid / n3, node = tid - el * n3;
+  const int e0 = blockIdx.x * NE;
+  const int e = e0 + el;
+  const bool valid = e < K;
+  const int i = node % n, j = (node / n) % n, k = node / n2;
+  load_ops<real, n>(sOp, ops, tid, T);
+  for (int t = tid; t < NE * 6; t += T) sES[t] = (e0 + t / 6 < K) ? elemSide[(size_t)e0 * 6 + t] : 0;
+  real Uo[NV], W[NV], jac[9], G[15], sj;
+  if (valid) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Uo[v] = U[((size_t)e * NV + v) * n3 + node];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) jac[c] = Ja[((size_t)e * 9 + c) * n3 + node];
+#pragma unroll
+    for (int c = 0; c < 15; ++c) G[c] = Gvol[((size_t)e * 15 + c) * n3 + node];
+    sj = sJ[(size_t)e * n3 + node];
+  } else {
+    Uo[0] = real(1); Uo[1] = Uo[2] = Uo[3] = real(0); Uo[4] = real(1);
+#pragma unroll
+    for (int c = 0; c < 9; ++c) jac[c] = real(0);
+#pragma unroll
+    for (int c = 0; c < 15; ++c) G[c] = real(0);
+    sj = real(0);
+  }
+  cons_to_prim(Uo, W, ph);
+  real* myb = sbuf + el * 15 * n3;
+  // lam_vol = -lam / J into the buffer
+#pragma unroll
+  for (int v = 0; v < NV; ++v) myb[v * n3 + node] = valid ? -lam[((size_t)e * NV + v) * n3 + node] * sj : real(0);
+  // face-gradient adjoints of the element's six faces (own slot)
+  __syncthreads();
+  for (int it = tid; it < NE * 6 * n2; it += T) {
+    const int el2 = it / (6 * n2);
+    const int r = it - el2 * 6 * n2;
+    const int s = r / n2, pq = r - s * n2;
+    if (e0 + el2 >= K) continue;
+    const int es = sES[el2 * 6 + s];
+    const int mpq = orient_pq(es_orient(es), n - 1, pq % n, pq / n);
+    const real* src = LGf + ((size_t)(es_slave(es) * S + es_side(es)) * 15) * n2 + mpq;
+#pragma unroll
+    for (int c = 0; c < 15; ++c) sF[((el2 * 6 + s) * 15 + c) * n2 + pq] = src[c * n2];
+  }
+  __syncthreads();
+  const real* sD = sOp;
+  // reverse of a7: lamFl[l][v] = (Dhat^T along l) lam_vol
+  real lamU[NV] = {0, 0, 0, 0, 0}, lamW[NV] = {0, 0, 0, 0, 0}, lamG[15];
+#pragma unroll
+  for (int c = 0; c < 15; ++c) lamG[c] = real(0);
+  {
+    real lFl[3][NV];
+#pragma unroll
+    for (int l = 0; l < 3; ++l)
+#pragma unroll
+      for (int v = 0; v < NV; ++v) lFl[l][v] = dhatT_line<real, n>(sD, myb + v * n3, l, i, j, k);
+    // reverse of a6: lam_d = sum_l Ja^l_d lamFl[l]; F_d = F^c_d - F^v_d
+    real lvisc[3][NV];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      real ld[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        ld[v] = jac[0 * 3 + d] * lFl[0][v] + jac[1 * 3 + d] * lFl[1][v] + jac[2 * 3 + d] * lFl[2][v];
+        lvisc[d][v] = -ld[v];
+      }
+      conv_vjp(Uo, W, d, ld, lamU, lamW);
+    }
+    visc_vjp(W, G, lvisc, ph, lamW, lamG);
+  }
+  // reverse of a4: face gradients = prolongation of G
+  {
+    const real* lm = sOp + n2;
+    const real* lp = sOp + n2 + n;
+    const real* Fe = sF + el * 6 * 15 * n2;
+    const int pq0 = j + n * k, pq1 = i + n * k, pq2 = i + n * j;
+    const real c0 = lm[i], c1 = lp[i], c2 = lm[j], c3 = lp[j], c4 = lm[k], c5 = lp[k];
+#pragma unroll
+    for (int c = 0; c < 15; ++c) {
+      lamG[c] += c0 * Fe[(0 * 15 + c) * n2 + pq0] + c1 * Fe[(1 * 15 + c) * n2 + pq0] +
+                 c2 * Fe[(2 * 15 + c) * n2 + pq1] + c3 * Fe[(3 * 15 + c) * n2 + pq1] +
+                 c4 * Fe[(4 * 15 + c) * n2 + pq2] + c5 * Fe[(5 * 15 + c) * n2 + pq2];
+    }
+  }
+  // reverse of a3: lam_lift = lamG / J ; W receives sum_d sum_l Ja^l_d (Dhat^T_l lam_lift^d)
+  __syncthreads();
+#pragma unroll
+  for (int c = 0; c < 15; ++c) myb[c * n3 + node] = lamG[c] * sj;
+  __syncthreads();
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+      const real a = jac[l * 3 + d];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) lamW[v] += a * dhatT_line<real, n>(sD, myb + (d * NV + v) * n3, l, i, j, k);
+    }
+  // lifting surface terms: lamWstar_s[v](pq) = sum_d n_d s_hat sigma sum_a lhat_a lam_lift^d_v(line)
+  {
+    const real* lhm = sOp + n2 + 2 * n;
+    const real* lhp = sOp + n2 + 3 * n;
+    for (int it = tid; it < NE * 6 * n2; it += T) {
+      const int el2 = it / (6 * n2);
+      const int r = it - el2 * 6 * n2;
+      const int s = r / n2, pq = r - s * n2;
+      if (e0 + el2 >= K) continue;
+      const int l = s >> 1;
+      const real* lv = (s & 1) ? lhp : lhm;
+      const int p = pq % n, q = pq / n;
+      const int es = sES[el2 * 6 + s];
+      const int side = es_side(es);
+      const int mpq = orient_pq(es_orient(es), n - 1, p, q);
+      const real* g = fgeo + ((size_t)side * 4) * n2 + mpq;
+      const real sc = es_slave(es) ? -g[3 * n2] : g[3 * n2];
+      const real nd[3] = {g[0] * sc, g[n2] * sc, g[2 * n2] * sc};
+      const real* b = sbuf + el2 * 15 * n3;
+      real* dst = LWs + ((size_t)(es_slave(es) * S + side) * NV) * n2 + mpq;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        real acc = real(0);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          real sdv = real(0);
+#pragma unroll
+          for (int a = 0; a < n; ++a) sdv += lv[a] * b[(d * NV + v) * n3 + vol_index(l, a, p, q, n)];
+          acc += nd[d] * sdv;
+        }
+        dst[v * n2] = acc;
+      }
+    }
+  }
+  // primitive map of the volume state
+  prim_vjp(W, lamW, ph, lamU);
+  if (valid) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) muv[((size_t)e * NV + v) * n3 + node] = lamU[v];
+  }
+}
+
+// side: BR1 mean and the primitive map of the face states -> adjoint of U_face
+template <typename real, int n>
+__global__ void __launch_bounds__(128) k_adj_side(const real* __restrict__ Wf, const real* __restrict__ LWs,
+                                                  real* __restrict__ LWf, int S, Phys<real> ph) {
+  constexpr int n2 = n * n;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= S * n2) return;
+  const int side = idx / n2, pq = idx - side * n2;
+#pragma unroll
+  for (int slot = 0; slot < 2; ++slot) {
+    real W[NV], lW[NV], lU[NV] = {0, 0, 0, 0, 0};
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const size_t g0 = ((size_t)side * NV + v) * n2 + pq, g1 = ((size_t)(S + side) * NV + v) * n2 + pq;
+      const size_t gs = slot ? g1 : g0;
+      W[v] = Wf[gs];
+      lW[v] = LWf[gs] + real(0.5) * (LWs[g0] + LWs[g1]);
+    }
+    prim_vjp(W, lW, ph, lU);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) LWf[((size_t)(slot * S + side) * NV + v) * n2 + pq] = lU[v];
+  }
+}
+
+// element: prolongation^T of the face-state adjoints, combine, scale/accumulate
+template <typename real, int n>
+__global__ void __launch_bounds__(Cfg<n>::T) k_adj_gather(const real* __restrict__ LUf, const int* __restrict__ elemSide,
+                                                           const real* __restrict__ muv, real* __restrict__ out,
+                                                           real scale, int accumulate, int K, int S, Ops<real> ops) {
+  using C = Cfg<n>;
+  constexpr int n2 = C::n2, n3 = C::n3, NE = C::NE, T = C::T;
+  __shared__ real sF[NE * 6 * NV * n2];
+  __shared__ real sOp[n2 + 4 * n];
+  __shared__ int sES[NE * 6];
+  const int tid = threadIdx.x;
+  const int el = tid / n3, node = tid - el * n3;
+  const int e0 = blockIdx.x * NE;
+  const int e = e0 + el;
+  const int i = node % n, j = (node / n) % n, k = node / n2;
+  load_ops<real, n>(sOp, ops, tid, T);
+  for (int t = tid; t < NE * 6; t += T) sES[t] = (e0 + t / 6 < K) ? elemSide[(size_t)e0 * 6 + t] : 0;
+  __syncthreads();
+  for (int it = tid; it < NE * 6 * n2; it += T) {
+    const int el2 = it / (6 * n2);
+    const int r = it - el2 * 6 * n2;
+    const int s = r / n2, pq = r - s * n2;
+    if (e0 + el2 >= K) continue;
+    const int es = sES[el2 * 6 + s];
+    const int mpq = orient_pq(es_orient(es), n - 1, pq % n, pq / n);
+    const real* src = LUf + ((size_t)(es_slave(es) * S + es_side(es)) * NV) * n2 + mpq;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) sF[((el2 * 6 + s) * NV + v) * n2 + pq] = src[v * n2];
+  }
+  __syncthreads();
+  if (e >= K) return;
+  const real* lm = sOp + n2;
+  const real* lp = sOp + n2 + n;
+  const real c0 = lm[i], c1 = lp[i], c2 = lm[j], c3 = lp[j], c4 = lm[k], c5 = lp[k];
+  const int pq0 = j + n * k, pq1 = i + n * k, pq2 = i + n * j;
+  const real* Fe = sF + el * 6 * NV * n2;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const size_t g = ((size_t)e * NV + v) * n3 + node;
+    const real m = muv[g] + c0 * Fe[(0 * NV + v) * n2 + pq0] + c1 * Fe[(1 * NV + v) * n2 + pq0] +
+                   c2 * Fe[(2 * NV + v) * n2 + pq1] + c3 * Fe[(3 * NV + v) * n2 + pq1] +
+                   c4 * Fe[(4 * NV + v) * n2 + pq2] + c5 * Fe[(5 * NV + v) * n2 + pq2];
+    out[g] = (accumulate ? out[g] : real(0)) + scale * m;
+  }
+}
+
+// y = a*y + b*x (elementwise)
+template <typename real>
+__global__ void k_axpby(real* __restrict__ y, const real* __restrict__ x, real a, real b, size_t count) {
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx < count) y[idx] = a * y[idx] + (x ? b * x[idx] : real(0));
+}
+
+// ---------------------------------------------------------------------------
+// launcher: forward recompute + reverse sweep
+// ---------------------------------------------------------------------------
+struct AdjScratch {
+  void *LF, *LWf, *LGf, *LWs, *muv;
+};
+
+inline AdjScratch adj_layout(const DevMesh& m, void* base, size_t rs) {
+  const size_t sf5 = 2 * (size_t)m.S * NV * m.n * m.n * rs, sf15 = 2 * (size_t)m.S * 15 * m.n * m.n * rs;
+  char* p = (char*)base;
+  AdjScratch a;
+  a.LF = p; p += sf5;
+  a.LWf = p; p += sf5;
+  a.LGf = p; p += sf15;
+  a.LWs = p; p += sf5;
+  a.muv = p;
+  return a;
+}
+
+template <typename real, int n>
+static cudaError_t rhs_adjoint_n(const DevMesh& m, const real* U, const real* lam, real* out, real scale,
+                                 int accumulate, const Ops<real>& ops, const Phys<real>& ph, void* scratch,
+                                 cudaStream_t st) {
+  using C = Cfg<n>;
+  const int grid = (m.K + C::NE - 1) / C::NE;
+  const int sgrid = (m.S * n * n + 127) / 128;
+  AdjScratch a = adj_layout(m, scratch, sizeof(real));
+  cudaError_t err;
+  // forward recompute of face states, face gradients and volume gradients
+  if ((err = prolong_n<real, n>(m, U, ops, ph, st)) != cudaSuccess) return err;
+  if ((err = lift_vol_n<real, n, 0>(m, U, ops, ph, 1, st)) != cudaSuccess) return err;
+  k_adj_lamface<real, n><<<grid, C::T, 0, st>>>(lam, (const real*)m.sJ, m.elemSide, (real*)a.LF, m.K, m.S, ops);
+  k_adj_face<real, n><<<sgrid, 128, 0, st>>>((const real*)m.Wf, (const real*)m.Gf, (const real*)m.fgeo,
+                                             (const real*)a.LF, (real*)a.LWf, (real*)a.LGf, m.S, ph);
+  constexpr size_t smem = adj_vol_smem<real, n>();
+  static bool attr = false;
+  if (!attr) {
+    if ((err = cudaFuncSetAttribute(k_adj_vol<real, n>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+        cudaSuccess)
+      return err;
+    attr = true;
+  }
+  k_adj_vol<real, n><<<grid, C::T, smem, st>>>(U, (const real*)m.Ja, (const real*)m.sJ, (const real*)m.Gvol,
+                                               (const real*)m.fgeo, m.elemSide, lam, (const real*)a.LGf,
+                                               (real*)a.LWs, (real*)a.muv, m.K, m.S, ops, ph);
+  k_adj_side<real, n><<<sgrid, 128, 0, st>>>((const real*)m.Wf, (const real*)a.LWs, (real*)a.LWf, m.S, ph);
+  k_adj_gather<real, n><<<grid, C::T, 0, st>>>((const real*)a.LWf, m.elemSide, (const real*)a.muv, out, scale,
+                                               accumulate, m.K, m.S, ops);
+  return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t launch_rhs_adjoint(const DevMesh& m, const real* U, const real* lam, real* out, real scale, int accumulate,
+                               const Ops<real>& ops, const Phys<real>& ph, void* scratch, cudaStream_t st) {
+  FLEXI_DISPATCH_N(m.n, return rhs_adjoint_n<real, NN>(m, U, lam, out, scale, accumulate, ops, ph, scratch, st));
+  return cudaSuccess;
+}
+
+template <typename real>
+cudaError_t launch_axpby(real* y, const real* x, real a, real b, size_t count, cudaStream_t st) {
+  k_axpby<real><<<(unsigned)((count + 255) / 256), 256, 0, st>>>(y, x, a, b, count);
+  return cudaGetLastError();
+}
+
+}  // namespace flexi

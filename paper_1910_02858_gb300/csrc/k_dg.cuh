@@ -15,6 +15,7 @@
 // from shared memory; the per-node results stay in registers.
 #pragma once
 #include "dg_common.cuh"
+#include "k_tc.cuh"
 #include "launch.h"
 
 namespace flexi {
@@ -145,7 +146,8 @@ __global__ void k_bc(const double* __restrict__ xbc, real* __restrict__ Wf, int 
 // ---------------------------------------------------------------------------
 // a2-a4, a6, a7: lifting, gradient prolongation, volume integral
 // ---------------------------------------------------------------------------
-template <typename real, int n>
+// SW: 0 line sweeps on the FP32/FP64 pipes; 1 TF32 3-pass mma; 2 BF16 3-term mma (float only)
+template <typename real, int n, int SW>
 __global__ void __launch_bounds__(Cfg<n>::T) k_lift_vol(
     const real* __restrict__ U, const real* __restrict__ Ja, const real* __restrict__ sJ,
     const real* __restrict__ Wf, const real* __restrict__ fgeo, const int* __restrict__ elemSide,
@@ -158,6 +160,7 @@ __global__ void __launch_bounds__(Cfg<n>::T) k_lift_vol(
   real* sQ = sbuf + NE * 15 * n3;                  // [NE][6][15][n2]  (v*3+d)
   real* sOp = sQ + NE * 6 * 15 * n2;               // DhatT, lm, lp, lhm, lhp
   int* sES = reinterpret_cast<int*>(sOp + n2 + 4 * n);
+  float* sOut = reinterpret_cast<float*>(sES + ((NE * 6 + 3) & ~3));  // [NE][5][n3] (SW != 0)
 
   const int tid = threadIdx.x;
   const int el = tid / n3, node = tid - el * n3;
@@ -184,6 +187,8 @@ __global__ void __launch_bounds__(Cfg<n>::T) k_lift_vol(
   }
   cons_to_prim(Uo, W, ph);
   __syncthreads();
+  BFrag<SW> bfr;
+  if constexpr (SW != 0) bfr = make_bfrag<n, SW>(reinterpret_cast<const float*>(sOp), tid & 31);
 
   // BR1 surface terms: Q = U* n_d s_hat with the element's outward normal
   for (int it = tid; it < NE * 6 * n2; it += T) {
@@ -228,7 +233,13 @@ __global__ void __launch_bounds__(Cfg<n>::T) k_lift_vol(
     real acc[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) acc[v] = real(0);
-    dhat_sweep3<real, n>(sD, myb, i, j, k, acc);
+    if constexpr (SW == 0) {
+      dhat_sweep3<real, n>(sD, myb, i, j, k, acc);
+    } else {
+      tc_sweep3<n, NE, SW>(reinterpret_cast<const float*>(sbuf), sOut, bfr, tid, T);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) acc[v] = sOut[(el * NV + v) * n3 + node];
+    }
     const real c0 = lhm[i], c1 = lhp[i], c2 = lhm[j], c3 = lhp[j], c4 = lhm[k], c5 = lhp[k];
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
@@ -293,17 +304,24 @@ __global__ void __launch_bounds__(Cfg<n>::T) k_lift_vol(
   real acc[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) acc[v] = real(0);
-  dhat_sweep3<real, n>(sD, myb, i, j, k, acc);
+  if constexpr (SW == 0) {
+    dhat_sweep3<real, n>(sD, myb, i, j, k, acc);
+  } else {
+    tc_sweep3<n, NE, SW>(reinterpret_cast<const float*>(sbuf), sOut, bfr, tid, T);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[v] = sOut[(el * NV + v) * n3 + node];
+  }
   if (valid) {
 #pragma unroll
     for (int v = 0; v < NV; ++v) Utv[((size_t)e * NV + v) * n3 + node] = acc[v];
   }
 }
 
-template <typename real, int n>
+template <typename real, int n, int SW>
 constexpr size_t lift_vol_smem() {
   using C = Cfg<n>;
-  return sizeof(real) * (C::NE * 15 * C::n3 + C::NE * 6 * 15 * C::n2 + C::n2 + 4 * n) + sizeof(int) * C::NE * 6;
+  return sizeof(real) * (C::NE * 15 * C::n3 + C::NE * 6 * 15 * C::n2 + C::n2 + 4 * n) +
+         sizeof(int) * ((C::NE * 6 + 3) & ~3) + (SW != 0 ? sizeof(float) * C::NE * NV * C::n3 : 0);
 }
 
 // ---------------------------------------------------------------------------
@@ -469,28 +487,36 @@ cudaError_t launch_bc(const DevMesh& m, double t, const Phys<real>& ph, cudaStre
   return cudaGetLastError();
 }
 
-template <typename real, int n>
+template <typename real, int n, int SW>
 static cudaError_t lift_vol_n(const DevMesh& m, const real* U, const Ops<real>& ops, const Phys<real>& ph,
                               int store_grad, cudaStream_t st) {
   using C = Cfg<n>;
-  constexpr size_t smem = lift_vol_smem<real, n>();
+  constexpr size_t smem = lift_vol_smem<real, n, SW>();
   static bool attr = false;
   if (!attr) {
-    cudaError_t err = cudaFuncSetAttribute(k_lift_vol<real, n>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t err =
+        cudaFuncSetAttribute(k_lift_vol<real, n, SW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     attr = true;
   }
   const int grid = (m.K + C::NE - 1) / C::NE;
-  k_lift_vol<real, n><<<grid, C::T, smem, st>>>(U, (const real*)m.Ja, (const real*)m.sJ, (const real*)m.Wf,
-                                                (const real*)m.fgeo, m.elemSide, (real*)m.Gf, (real*)m.Utv,
-                                                store_grad ? (real*)m.Gvol : nullptr, m.K, m.S, ops, ph);
+  k_lift_vol<real, n, SW><<<grid, C::T, smem, st>>>(U, (const real*)m.Ja, (const real*)m.sJ, (const real*)m.Wf,
+                                                    (const real*)m.fgeo, m.elemSide, (real*)m.Gf, (real*)m.Utv,
+                                                    store_grad ? (real*)m.Gvol : nullptr, m.K, m.S, ops, ph);
   return cudaGetLastError();
 }
 
 template <typename real>
 cudaError_t launch_lift_vol(const DevMesh& m, const real* U, const Ops<real>& ops, const Phys<real>& ph,
                             int store_grad, cudaStream_t st) {
-  FLEXI_DISPATCH_N(m.n, return lift_vol_n<real, NN>(m, U, ops, ph, store_grad, st));
+  if constexpr (sizeof(real) == 4) {
+    if (m.sweep_mode == 1) {
+      FLEXI_DISPATCH_N(m.n, return lift_vol_n<real, NN, 1>(m, U, ops, ph, store_grad, st));
+    } else if (m.sweep_mode == 2) {
+      FLEXI_DISPATCH_N(m.n, return lift_vol_n<real, NN, 2>(m, U, ops, ph, store_grad, st));
+    }
+  }
+  FLEXI_DISPATCH_N(m.n, return lift_vol_n<real, NN, 0>(m, U, ops, ph, store_grad, st));
   return cudaSuccess;
 }
 
