@@ -199,11 +199,13 @@ def reference_arm(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the FP32 and adjoint extra measurements")
+    ap.add_argument("--form", default="fp64", choices=["fp64", "fp32", "tf32x3", "bf16x3"],
+                    help="arithmetic form of the timed workload (default: the FP64 headline)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -235,10 +237,11 @@ def main():
     mesh = wl.box_mesh((16, 16, 16), Ngeo=1)
     x = mesh.node_coords(N, 0)
     U0 = wl.taylor_green(x)
-    cfg = SolverConfig(N=N, riemann=F.RIEMANN_HLLC, precision=F.FP64)
+    prec = {"fp64": F.FP64, "fp32": F.FP32, "tf32x3": F.FP32_TF32, "bf16x3": F.FP32_BF16}[args.form]
+    cfg = SolverConfig(N=N, riemann=F.RIEMANN_HLLC, precision=prec)
     s = Solver(cfg, mesh.coords, mesh.conn, device=dev)
     dof = s.query(F.Q_DOF)
-    U = torch.tensor(U0, device=dev)
+    U = torch.tensor(U0, device=dev, dtype=s.dtype)
     dU = torch.zeros_like(U)
     dt = s.reduce(U)["dt_max"]
     stream = torch.cuda.current_stream(dev)
@@ -278,21 +281,32 @@ def main():
     ms_step = ms_total / args.steps
     pid = ms_total * 1e6 / (args.steps * NSTAGES * dof * world)  # whole job
 
-    # roofline of the dominant kernel (lifting + volume), FP64 ALU-bound
+    # roofline of the dominant kernel (lifting + volume): FP64 form ALU-bound (FP64 pipe),
+    # FP32 forms HBM-bound
     n = N + 1
-    bytes_stage, bytes_lv, flops_lv = algorithmic_per_dof(n, 8)
+    word = 8 if args.form == "fp64" else 4
+    bytes_stage, bytes_lv, flops_lv = algorithmic_per_dof(n, word)
     lv_ms, lv_cnt = ktimes["lift_vol"]
     lv_avg_s = lv_ms / max(lv_cnt, 1) * 1e-3
-    achieved_tflops = flops_lv * dof / lv_avg_s / 1e12
-    roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved_tflops / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "k_lift_vol<double,8>",
-                "peak_source": "derived: 152 SM x 4 FP64 flop/clk x 2070 MHz (nominal 1.25 TFLOP/s)",
-                "kernel_share": lv_ms / max(sum(v[0] for v in ktimes.values()), 1e-9)}
+    share = lv_ms / max(sum(v[0] for v in ktimes.values()), 1e-9)
+    if args.form == "fp64":
+        achieved_tflops = flops_lv * dof / lv_avg_s / 1e12
+        roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved_tflops / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "k_lift_vol<double,8>",
+                    "peak_source": "derived: 152 SM x 4 FP64 flop/clk x 2070 MHz (nominal 1.25 TFLOP/s)",
+                    "kernel_share": share}
+    else:
+        hbm = peaks().get("hbm_gbs", 6800.0)
+        achieved = bytes_lv * dof / lv_avg_s / 1e9
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                    "traffic": None, "kernel": f"k_lift_vol<float,8,{args.form}>",
+                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks() else "fallback 6.8 TB/s",
+                    "kernel_share": share}
     step_bytes_gbs = bytes_stage * dof * NSTAGES / (ms_step * 1e-3) / 1e9
     kernels = {k: {"ms_per_launch": (v[0] / v[1]) if v[1] else 0.0, "launches": v[1]} for k, v in ktimes.items() if v[1]}
 
     # end to end through the public API with host buffers (H2D + step + D2H per step)
-    Uh = torch.tensor(U0).pin_memory()
+    Uh = torch.tensor(U0, dtype=s.dtype).pin_memory()
     F.flexi_rk_run_host(s.ctx, Uh, 1, 0.0, dt, stream)
     barrier()
     t0 = time.perf_counter()
@@ -305,11 +319,12 @@ def main():
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         e2e_s = float(tt.item())
     e2e_pid = e2e_s * 1e9 / (e2e_steps * NSTAGES * dof * world)
-    ubytes = U.numel() * 8
+    ubytes = U.numel() * U.element_size()
 
     line = {"metric": METRIC, "value": pid, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": dict(WORKLOAD, dt=dt),
+            "vs_baseline": None, "dtype": "f64" if args.form == "fp64" else "f32", "data": "synthetic",
+            "config": dict(WORKLOAD, dt=dt, form=args.form),
             "clocks": clk.summary(), "gpu_launches": launches_per_step * args.steps,
             "e2e": {"value": e2e_pid, "unit": UNIT, "h2d_bytes_per_step": ubytes, "d2h_bytes_per_step": ubytes},
             "roofline": roofline, "dof_updates_per_s": dof * world / (pid * 1e-9 * dof * world) if pid else None,
@@ -330,6 +345,18 @@ def main():
     return 0
 
 
+def rel_err_per_var(U, Uref):
+    """Relative L2 error per conserved variable; the momentum components are
+    normalised by the norm of the whole momentum vector (the Taylor-Green
+    w-momentum starts at zero)."""
+    d = (U.double() - Uref).transpose(0, 1).reshape(5, -1).norm(dim=1)
+    r = Uref.transpose(0, 1).reshape(5, -1).norm(dim=1)
+    rm = r[1:4].norm()
+    r = r.clone()
+    r[1:4] = rm
+    return (d / r).tolist()
+
+
 def extras(args, s64, U0, mesh, dt, dev, F, wl, Solver, SolverConfig, torch, np):
     """FP32 forms on the same workload (PID and error vs FP64 after the same
     number of steps) and the adjoint/forward cost ratio."""
@@ -337,7 +364,7 @@ def extras(args, s64, U0, mesh, dt, dev, F, wl, Solver, SolverConfig, torch, np)
     nsteps = 20
     U64 = torch.tensor(U0, device=dev)
     s64.run(U64, nsteps, dt)
-    for name, prec in (("fp32", F.FP32), ("fp32_tf32", F.FP32_TF32), ("fp32_bf16", F.FP32_BF16)):
+    for name, prec in (("fp32", F.FP32), ("fp32_tf32x3", F.FP32_TF32), ("fp32_bf16x3", F.FP32_BF16)):
         try:
             s = Solver(SolverConfig(N=7, riemann=F.RIEMANN_HLLC, precision=prec), mesh.coords, mesh.conn, device=dev)
         except Exception as exc:
@@ -350,6 +377,7 @@ def extras(args, s64, U0, mesh, dt, dev, F, wl, Solver, SolverConfig, torch, np)
                 s.step(U, dU, 0.0, dt)
             U = torch.tensor(U0, device=dev, dtype=torch.float32)
             dU.zero_()
+            F.flexi_profile(s.ctx, True)
             torch.cuda.synchronize(dev)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
@@ -358,16 +386,67 @@ def extras(args, s64, U0, mesh, dt, dev, F, wl, Solver, SolverConfig, torch, np)
             e1.record()
             torch.cuda.synchronize(dev)
             ms = e0.elapsed_time(e1)
+            kt = F.flexi_kernel_times(s.ctx, reset=True)
+            F.flexi_profile(s.ctx, False)
             dof = s.query(F.Q_DOF)
-            d = (U.double() - U64).transpose(0, 1).reshape(5, -1).norm(dim=1)
-            r = U64.transpose(0, 1).reshape(5, -1).norm(dim=1)
+            n = 8
+            bytes_stage = (46.0 + 117.0 * 3.0 / n) * 4 * dof
+            lv = kt["lift_vol"][0] / max(kt["lift_vol"][1], 1)
             out[name] = {"pid": ms * 1e6 / (nsteps * NSTAGES * dof), "steps": nsteps,
-                         "rel_l2_err_vs_fp64": (d / r).tolist()}
+                         "rel_l2_err_vs_fp64": rel_err_per_var(U, U64),
+                         "step_algorithmic_hbm_gbs": bytes_stage * NSTAGES * nsteps / (ms * 1e-3) / 1e9,
+                         "lift_vol_ms_per_launch": lv,
+                         "lift_vol_hbm_gbs": (20.0 + 48.0 * 3.0 / n) * 4 * dof / (lv * 1e-3) / 1e9}
         except Exception as exc:
             out[name] = {"error": str(exc)}
         finally:
             s.close()
+    try:
+        out["adjoint"] = adjoint_ratio(dev, F, wl, Solver, SolverConfig, torch)
+    except Exception as exc:
+        out["adjoint"] = {"error": repr(exc)}
     return out
+
+
+def adjoint_ratio(dev, F, wl, Solver, SolverConfig, torch):
+    """Cost of dJ/dU0 (checkpointed forward + recompute + reverse sweep) over the
+    cost of the plain forward run, on the adjoint workload: Taylor-Green Re = 400,
+    8^3, N = 5, Roe with smoothed |lambda|, 40 steps of dt = 1e-3, checkpoints
+    every 20 steps; and the per-step ratio at N = 7, 16^3."""
+    from paper_1910_02858_gb300.adjoint import final_state
+
+    res = {}
+    for label, nel, N, nsteps in (("c5_8^3_N5_40steps", 8, 5, 40), ("16^3_N7_10steps", 16, 7, 10)):
+        mesh = wl.box_mesh((nel,) * 3, Ngeo=1)
+        s = Solver(SolverConfig(N=N, riemann=F.RIEMANN_ROE_SMOOTH, mu=1 / 400.0), mesh.coords, mesh.conn, device=dev)
+        U0 = torch.tensor(wl.taylor_green(mesh.node_coords(N, 0)), device=dev)
+        dt = 1e-3
+        lam = torch.randn_like(U0)
+
+        def fwd():
+            U = U0.clone()
+            s.run(U, nsteps, dt)
+            return U
+
+        def grad():
+            U0g = U0.clone().requires_grad_(True)
+            UT = final_state(U0g, s, nsteps, dt, 0.0, 20)
+            UT.backward(lam)
+            return U0g.grad
+
+        for f in (fwd, grad):
+            f()
+        times = {}
+        for name, f in (("forward", fwd), ("gradient", grad)):
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            f()
+            torch.cuda.synchronize(dev)
+            times[name] = time.perf_counter() - t0
+        res[label] = {"forward_ms": times["forward"] * 1e3, "gradient_ms": times["gradient"] * 1e3,
+                      "ratio": times["gradient"] / times["forward"]}
+        s.close()
+    return res
 
 
 if __name__ == "__main__":

@@ -58,8 +58,8 @@ enum { FLEXI_NODES_GAUSS = 0, FLEXI_NODES_LOBATTO = 1 };
  * |lambda| by (lambda^2 + delta^2)/(2 delta) below delta = 0.1 c (C^1 operator). */
 enum { FLEXI_RIEMANN_ROE = 0, FLEXI_RIEMANN_HLLC = 1, FLEXI_RIEMANN_ROE_SMOOTH = 2 };
 /* Arithmetic forms: FP64; FP32 storage+flux math with FP32 line sweeps; FP32
- * with the D-matrix line sweeps on tensor cores in TF32 (3-pass split) or BF16
- * (3-term split), accumulating in FP32. */
+ * with the D-matrix line sweeps on tensor cores in TF32 or BF16, each operand
+ * split into three terms of the narrow type (six products, FP32 accumulation). */
 enum { FLEXI_FP64 = 0, FLEXI_FP32 = 1, FLEXI_FP32_TF32 = 2, FLEXI_FP32_BF16 = 3 };
 /* Exact states for Dirichlet sides (and the manufactured source term). */
 enum { FLEXI_EXACT_TGV = 0, FLEXI_EXACT_FREESTREAM = 1, FLEXI_EXACT_MANUFACTURED = 2 };

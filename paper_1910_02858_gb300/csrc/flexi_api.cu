@@ -423,7 +423,11 @@ flexi_status mesh_init_impl(flexi_ctx* c, const flexi_params* p, int K, const do
     CK(convert_f64_to_f32(c->fgeo64, c->fgeo32, (size_t)S * 4 * n2, st));
     c->m.Ja = c->Ja32; c->m.sJ = c->sJ32; c->m.fgeo = c->fgeo32;
   }
-  unsigned char *Wf, *Gf, *Ff, *Utv, *Us, *dUs;
+  unsigned char *Wf, *Gf, *Ff, *Utv, *Us, *dUs, *Gvol, *adj;
+  AL(Gvol, (size_t)K * 15 * n3 * rs);
+  c->m.Gvol = Gvol;
+  AL(adj, adjoint_scratch_bytes(c->m, rs));
+  c->adj_scratch = adj;
   AL(Wf, 2 * (size_t)S * NV * n2 * rs);
   AL(Gf, 2 * (size_t)S * 15 * n2 * rs);
   AL(Ff, (size_t)S * NV * n2 * rs);
@@ -439,6 +443,33 @@ flexi_status mesh_init_impl(flexi_ctx* c, const flexi_params* p, int K, const do
   CK(cudaStreamSynchronize(st));
 #undef AL
 #undef TA
+  return FLEXI_OK;
+}
+
+template <typename real>
+flexi_status do_rhs_adjoint(flexi_ctx* c, const real* U, const real* lam, real* out, real scale, int accumulate,
+                            cudaStream_t st) {
+  Prof pr(c, KC_ADJ, st);
+  CK(launch_rhs_adjoint<real>(c->m, U, lam, out, scale, accumulate, ops_of<real>(c), ph_of<real>(c), c->adj_scratch,
+                              st));
+  return FLEXI_OK;
+}
+
+// reverse of one LSERK4(5) step (Williamson 2N form):
+//   for k = 5..1: lam_dU += B_k lamU; lamU += dt (dL/dU(U_{k-1}))^T lam_dU; lam_dU = A_k lam_dU
+template <typename real>
+flexi_status do_adjoint_step(flexi_ctx* c, const real* stages, real* lamU, real* lam_dU, double dt, cudaStream_t st) {
+  const size_t nU = (size_t)c->K * NV * c->n3;
+  for (int k = 4; k >= 0; --k) {
+    {
+      Prof pr(c, KC_OTHER, st);
+      CK(launch_axpby<real>(lam_dU, lamU, real(1), (real)RK_B[k], nU, st));
+    }
+    flexi_status s = do_rhs_adjoint<real>(c, stages + k * nU, lam_dU, lamU, (real)dt, 1, st);
+    if (s != FLEXI_OK) return s;
+    Prof pr(c, KC_OTHER, st);
+    CK(launch_axpby<real>(lam_dU, nullptr, (real)RK_A[k], real(0), nU, st));
+  }
   return FLEXI_OK;
 }
 
@@ -469,6 +500,13 @@ flexi_status do_reduce(flexi_ctx* c, const void* U, const void* Ut, double cfl, 
 
 }  // namespace
 
+namespace flexi {
+size_t adjoint_scratch_bytes(const DevMesh& m, size_t rs) {
+  const size_t n2 = (size_t)m.n * m.n, n3 = n2 * m.n;
+  return rs * (4 * 2 * (size_t)m.S * NV * n2 + 2 * (size_t)m.S * 15 * n2 + (size_t)m.K * NV * n3);
+}
+}  // namespace flexi
+
 // ============================================================================
 // C ABI
 // ============================================================================
@@ -496,8 +534,8 @@ void flexi_destroy(flexi_ctx* c) {
   }
   for (void* p : c->allocs) cudaFree(p);
   if (c->partial_host) cudaFreeHost(c->partial_host);
-  if (c->adj_scratch) cudaFree(c->adj_scratch);
   delete c;
+  (void)cudaGetLastError();  // leave no error of this cleanup behind for the caller's next call
 }
 
 flexi_status flexi_mesh_init(flexi_ctx** out, const flexi_params* p, int K, const double* coords,
@@ -544,15 +582,27 @@ flexi_status flexi_rk_step_stages(flexi_ctx* c, void* U, void* dU, double t, dou
                  : do_rk_step<float>(c, (float*)U, (float*)dU, t, dt, (float*)U_stages, st);
 }
 
+static bool adjoint_supported(const flexi_ctx* c) {
+  return c->nBC == 0 && c->p.riemann != FLEXI_RIEMANN_HLLC && !c->p.source;
+}
+
 flexi_status flexi_adjoint_step(flexi_ctx* c, const void* U_stages, void* lamU, void* lam_dU, double t, double dt,
                                 void* stream) {
   if (c == nullptr || U_stages == nullptr || lamU == nullptr || lam_dU == nullptr) return FLEXI_EINVAL;
-  return FLEXI_EUNSUPPORTED;
+  if (!adjoint_supported(c)) return FLEXI_EUNSUPPORTED;
+  (void)t;  // the operator is autonomous on periodic meshes without source terms
+  cudaStream_t st = (cudaStream_t)stream;
+  return c->fp64 ? do_adjoint_step<double>(c, (const double*)U_stages, (double*)lamU, (double*)lam_dU, dt, st)
+                 : do_adjoint_step<float>(c, (const float*)U_stages, (float*)lamU, (float*)lam_dU, dt, st);
 }
 
 flexi_status flexi_rhs_adjoint(flexi_ctx* c, const void* U, const void* lam, void* out, double t, void* stream) {
   if (c == nullptr || U == nullptr || lam == nullptr || out == nullptr) return FLEXI_EINVAL;
-  return FLEXI_EUNSUPPORTED;
+  if (!adjoint_supported(c)) return FLEXI_EUNSUPPORTED;
+  (void)t;
+  cudaStream_t st = (cudaStream_t)stream;
+  return c->fp64 ? do_rhs_adjoint<double>(c, (const double*)U, (const double*)lam, (double*)out, 1.0, 0, st)
+                 : do_rhs_adjoint<float>(c, (const float*)U, (const float*)lam, (float*)out, 1.0f, 0, st);
 }
 
 flexi_status flexi_rk_run_host(flexi_ctx* c, void* U_host, int nsteps, double t0, double dt, void* stream) {

@@ -146,7 +146,7 @@ __global__ void k_bc(const double* __restrict__ xbc, real* __restrict__ Wf, int 
 // ---------------------------------------------------------------------------
 // a2-a4, a6, a7: lifting, gradient prolongation, volume integral
 // ---------------------------------------------------------------------------
-// SW: 0 line sweeps on the FP32/FP64 pipes; 1 TF32 3-pass mma; 2 BF16 3-term mma (float only)
+// SW: 0 line sweeps on the FP32/FP64 pipes; 1 TF32 and 2 BF16 3-term split mma (float only)
 template <typename real, int n, int SW>
 __global__ void __launch_bounds__(Cfg<n>::T) k_lift_vol(
     const real* __restrict__ U, const real* __restrict__ Ja, const real* __restrict__ sJ,

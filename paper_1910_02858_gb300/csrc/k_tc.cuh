@@ -7,12 +7,13 @@
 // mma.sync (m16n8k8 TF32 or m16n8k16 BF16) with FP32 accumulation; results are
 // added into a shared per-node accumulator, one direction at a time.
 //
-// Split precision: TF32 keeps 11 significant bits, so each operand is split
-// into hi + lo (both TF32) and three products hi*hi + hi*lo + lo*hi are formed
-// (the lo*lo term, ~2^-22 relative, is dropped).  BF16 keeps 8 bits, so each
-// operand is split into three BF16 terms x1 + x2 + x3 and the six products of
-// total order <= 2 are formed, packed pairwise into the K = 16 dimension:
-// [A1|A2]x[B1;B2], [A1|A2]x[B2;B1], [A1|A3]x[B3;B1].
+// Split precision: TF32 keeps 11 significant bits and BF16 8, so each operand
+// is split into three terms x1 + x2 + x3 of the narrow type (33 resp. 24
+// bits, i.e. FP32-equivalent), and the six products of total order <= 2
+// (A1B1, A1B2, A2B1, A1B3, A2B2, A3B1) are formed and accumulated in FP32,
+// smallest first.  TF32 (m16n8k8) issues them as six mma; BF16 (m16n8k16)
+// packs them pairwise into the K = 16 dimension:
+// [A1|A3]x[B3;B1], [A1|A2]x[B2;B1], [A1|A2]x[B1;B2].
 #pragma once
 #include <cuda_bf16.h>
 
@@ -48,6 +49,13 @@ __device__ __forceinline__ uint32_t pack_bf16(float x0, float x1) {
   return *reinterpret_cast<uint32_t*>(&h);
 }
 
+__device__ __forceinline__ void split3_tf32(float x, uint32_t& x1, uint32_t& x2, uint32_t& x3) {
+  x1 = to_tf32(x);
+  const float r1 = x - __uint_as_float(x1);
+  x2 = to_tf32(r1);
+  x3 = to_tf32(r1 - __uint_as_float(x2));
+}
+
 __device__ __forceinline__ void split3_bf16(float x, float& x1, float& x2, float& x3) {
   x1 = __bfloat162float(__float2bfloat16_rn(x));
   const float r1 = x - x1;
@@ -67,13 +75,9 @@ __device__ __forceinline__ BFrag<SW> make_bfrag(const float* sD, int lane) {
   BFrag<SW> f;
   auto B = [&](int a, int i) -> float { return (a < n && i < n) ? sD[a * n + i] : 0.f; };
   if (SW == 1) {
-    const float b0 = B(tig, gid), b1 = B(tig + 4, gid);
-    const uint32_t h0 = to_tf32(b0), h1 = to_tf32(b1);
-    f.r[0] = h0;
-    f.r[1] = h1;
-    f.r[2] = to_tf32(b0 - __uint_as_float(h0));
-    f.r[3] = to_tf32(b1 - __uint_as_float(h1));
-    f.r[4] = f.r[5] = 0u;
+    // r[2t], r[2t+1]: term t of the rows (tig, tig + 4) at column gid
+    split3_tf32(B(tig, gid), f.r[0], f.r[2], f.r[4]);
+    split3_tf32(B(tig + 4, gid), f.r[1], f.r[3], f.r[5]);
   } else {
     float p0[3], p1[3];  // rows a = 2tig, 2tig+1 at column gid, three split terms
     split3_bf16(B(2 * tig, gid), p0[0], p0[1], p0[2]);
@@ -122,14 +126,18 @@ __device__ __forceinline__ void tc_sweep3(const float* __restrict__ buf, float* 
         };
         float c[4] = {0.f, 0.f, 0.f, 0.f};
         if (SW == 1) {
-          const float x00 = Aval(0, tig), x10 = Aval(1, tig), x01 = Aval(0, tig + 4), x11 = Aval(1, tig + 4);
-          uint32_t ah[4] = {to_tf32(x00), to_tf32(x10), to_tf32(x01), to_tf32(x11)};
-          uint32_t al[4] = {to_tf32(x00 - __uint_as_float(ah[0])), to_tf32(x10 - __uint_as_float(ah[1])),
-                            to_tf32(x01 - __uint_as_float(ah[2])), to_tf32(x11 - __uint_as_float(ah[3]))};
-          const uint32_t bh[2] = {bf.r[0], bf.r[1]}, bl[2] = {bf.r[2], bf.r[3]};
-          mma_tf32(c, al, bh);
-          mma_tf32(c, ah, bl);
-          mma_tf32(c, ah, bh);
+          uint32_t a[3][4];  // a[term][reg]: regs (row gid, col tig), (gid+8, tig), (gid, tig+4), (gid+8, tig+4)
+          split3_tf32(Aval(0, tig), a[0][0], a[1][0], a[2][0]);
+          split3_tf32(Aval(1, tig), a[0][1], a[1][1], a[2][1]);
+          split3_tf32(Aval(0, tig + 4), a[0][2], a[1][2], a[2][2]);
+          split3_tf32(Aval(1, tig + 4), a[0][3], a[1][3], a[2][3]);
+          const uint32_t b1[2] = {bf.r[0], bf.r[1]}, b2[2] = {bf.r[2], bf.r[3]}, b3[2] = {bf.r[4], bf.r[5]};
+          mma_tf32(c, a[2], b1);  // A3 B1
+          mma_tf32(c, a[1], b2);  // A2 B2
+          mma_tf32(c, a[0], b3);  // A1 B3
+          mma_tf32(c, a[1], b1);  // A2 B1
+          mma_tf32(c, a[0], b2);  // A1 B2
+          mma_tf32(c, a[0], b1);  // A1 B1
         } else {
           float s00[3], s01[3], s10[3], s11[3];  // rows gid / gid+8, cols 2tig / 2tig+1
           split3_bf16(Aval(0, 2 * tig), s00[0], s00[1], s00[2]);

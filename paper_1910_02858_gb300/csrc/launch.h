@@ -59,6 +59,8 @@ cudaError_t launch_rhs_adjoint(const DevMesh& m, const real* U, const real* lam,
                                int accumulate, const Ops<real>& ops, const Phys<real>& ph, void* scratch,
                                cudaStream_t st);
 size_t adjoint_scratch_bytes(const DevMesh& m, size_t real_size);
+template <typename real>
+cudaError_t launch_axpby(real* y, const real* x, real a, real b, size_t count, cudaStream_t st);
 
 // reductions (always FP64 accumulation)
 template <typename real>

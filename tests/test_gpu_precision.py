@@ -6,7 +6,9 @@ Right-hand sides are compared with the FP64 oracle using the tolerance of
 test_gpu_parity scaled to FP32 rounding (unit roundoff 2^-24 instead of
 2^-53, a factor 2^29), and states after 100 steps of the C3 workload
 (Taylor-Green, 32^3, N = 5) against the FP64 CUDA path, with the 1e-5
-relative L2 budget per conserved variable.
+relative L2 budget per conserved variable (momentum components measured
+against the norm of the momentum vector, since the Taylor-Green w-momentum
+starts at zero).
 """
 import numpy as np
 import pytest
@@ -59,6 +61,7 @@ def test_c3_fp32_forms_100_steps_vs_fp64():
         s.run(U, 100, dt)
         d = (U.double() - U64).transpose(0, 1).reshape(5, -1).norm(dim=1)
         r = U64.transpose(0, 1).reshape(5, -1).norm(dim=1)
+        r[1:4] = r[1:4].norm()  # momentum components against the momentum vector (w starts at 0)
         errs[form] = (d / r).tolist()
         ke = s.reduce(U)["kinetic_energy"]
         errs[form + "_ke"] = abs(ke - ke64) / ke64
