@@ -30,6 +30,31 @@ struct Phys {
   int bc_exact;
 };
 
+// Thread-block configuration of the element kernels: one thread per volume
+// node, NE elements per CTA (at least 64 threads).  Staged element fields use
+// i-lines padded to P = n + 1 entries (n3p per field) to spread shared-memory banks.
+template <int n>
+struct Cfg {
+  static constexpr int n2 = n * n;
+  static constexpr int n3 = n * n * n;
+  static constexpr int NE = n3 >= 64 ? 1 : (64 + n3 - 1) / n3;
+  static constexpr int T = NE * n3;
+  static constexpr int P = n + 1;
+  static constexpr int n3p = P * n * n;
+};
+
+// padded shared-memory offset of node (i, j, k)
+template <int n>
+__device__ __forceinline__ int pidx(int i, int j, int k) {
+  return i + (n + 1) * (j + n * k);
+}
+
+// padded offset of face node (p, q) at position a along the face normal direction l
+template <int n>
+__device__ __forceinline__ int pvol_index(int l, int a, int p, int q) {
+  return l == 0 ? pidx<n>(a, p, q) : (l == 1 ? pidx<n>(p, a, q) : pidx<n>(p, q, a));
+}
+
 // elemSide packing: (side << 4) | (slave << 3) | orient(local -> master frame)
 __host__ __device__ __forceinline__ int es_side(int v) { return v >> 4; }
 __host__ __device__ __forceinline__ int es_slave(int v) { return (v >> 3) & 1; }

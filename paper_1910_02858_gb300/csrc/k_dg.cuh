@@ -20,14 +20,6 @@
 
 namespace flexi {
 
-template <int n>
-struct Cfg {
-  static constexpr int n2 = n * n;
-  static constexpr int n3 = n * n * n;
-  static constexpr int NE = n3 >= 64 ? 1 : (64 + n3 - 1) / n3;
-  static constexpr int T = NE * n3;
-};
-
 // shared copy of the 1-D operators: DhatT[n*n], lm, lp, lhm, lhp
 template <typename real, int n>
 __device__ __forceinline__ void load_ops(real* s, const Ops<real>& ops, int tid, int T) {
@@ -40,20 +32,60 @@ __device__ __forceinline__ void load_ops(real* s, const Ops<real>& ops, int tid,
   }
 }
 
-// sum_a Dhat[i][a] f0[a,j,k] + Dhat[j][a] f1[i,a,k] + Dhat[k][a] f2[i,j,a] for NV fields each
+// Three D_hat line sweeps of the 15 staged fields of every element of the CTA:
+//   out[el][v][node] = sum_l sum_a Dhat[i_l][a] buf[el][l*5+v][node with index_l = a].
+// One thread per line: the line's n values are read once from shared memory and
+// D_hat comes from the kernel-parameter bank at compile-time offsets.  The three
+// directions accumulate into out one after the other.  Block-wide; ends synced.
 template <typename real, int n>
-__device__ __forceinline__ void dhat_sweep3(const real* __restrict__ sD, const real* __restrict__ buf, int i, int j,
+__device__ __forceinline__ void line_sweep3(const real* __restrict__ buf, real* __restrict__ out,
+                                            const Ops<real>& ops, int tid) {
+  using C = Cfg<n>;
+  constexpr int n2 = C::n2, n3p = C::n3p, P = C::P, NE = C::NE, T = C::T;
+  constexpr int L = NE * NV * n2;
+#pragma unroll 1
+  for (int l = 0; l < 3; ++l) {
+    const int stride = l == 0 ? 1 : (l == 1 ? P : P * n);
+    for (int it = tid; it < L; it += T) {
+      const int el = it / (NV * n2);
+      const int r = it - el * NV * n2;
+      const int v = r / n2, line = r - v * n2;
+      const int a0 = line % n, a1 = line / n;  // free indices in increasing direction order
+      const int base = l == 0 ? P * line : (l == 1 ? a0 + P * n * a1 : a0 + P * a1);
+      const real* src = buf + (el * 15 + l * NV + v) * n3p + base;
+      real x[n];
+#pragma unroll
+      for (int a = 0; a < n; ++a) x[a] = src[a * stride];
+      real* dst = out + (el * NV + v) * n3p + base;
+#pragma unroll
+      for (int ii = 0; ii < n; ++ii) {
+        real y = real(0);
+#pragma unroll
+        for (int a = 0; a < n; ++a) y += ops.DhatT[a * n + ii] * x[a];
+        dst[ii * stride] = (l == 0) ? y : dst[ii * stride] + y;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Per-node form of the same three sweeps (used by the FP64 form, which is bound
+// by the FP64 pipe and short of registers for whole lines): the thread of node
+// (i,j,k) accumulates sum_a Dhat[i][a] f0(a,j,k) + Dhat[j][a] f1(i,a,k) +
+// Dhat[k][a] f2(i,j,a) for the 5 variables, reading the padded staged fields.
+template <typename real, int n>
+__device__ __forceinline__ void node_sweep3(const real* __restrict__ sD, const real* __restrict__ buf, int i, int j,
                                             int k, real acc[NV]) {
-  constexpr int n2 = n * n, n3 = n * n * n;
+  constexpr int n3p = Cfg<n>::n3p;
 #pragma unroll
   for (int a = 0; a < n; ++a) {
     const real d0 = sD[a * n + i], d1 = sD[a * n + j], d2 = sD[a * n + k];
-    const int i0 = a + n * j + n2 * k, i1 = i + n * a + n2 * k, i2 = i + n * j + n2 * a;
+    const int i0 = pidx<n>(a, j, k), i1 = pidx<n>(i, a, k), i2 = pidx<n>(i, j, a);
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      acc[v] += d0 * buf[v * n3 + i0];
-      acc[v] += d1 * buf[(NV + v) * n3 + i1];
-      acc[v] += d2 * buf[(2 * NV + v) * n3 + i2];
+      acc[v] += d0 * buf[v * n3p + i0];
+      acc[v] += d1 * buf[(NV + v) * n3p + i1];
+      acc[v] += d2 * buf[(2 * NV + v) * n3p + i2];
     }
   }
 }
@@ -154,13 +186,14 @@ __global__ void __launch_bounds__(Cfg<n>::T) k_lift_vol(
     real* __restrict__ Gf, real* __restrict__ Utv, real* __restrict__ Gvol, int K, int S, Ops<real> ops,
     Phys<real> ph) {
   using C = Cfg<n>;
-  constexpr int n2 = C::n2, n3 = C::n3, NE = C::NE, T = C::T;
+  constexpr int n2 = C::n2, n3 = C::n3, NE = C::NE, T = C::T, n3p = C::n3p;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  real* sbuf = reinterpret_cast<real*>(smem_raw);  // [NE][15][n3]
-  real* sQ = sbuf + NE * 15 * n3;                  // [NE][6][15][n2]  (v*3+d)
+  real* sbuf = reinterpret_cast<real*>(smem_raw);  // [NE][15][n3p] staged fields (padded lines)
+  constexpr int nout = (sizeof(real) == 8 && SW == 0) ? 0 : NE * NV * n3p;
+  real* sOut = sbuf + NE * 15 * n3p;               // [NE][5][n3p]  sweep results (not for FP64)
+  real* sQ = sOut + nout;                          // [NE][6][15][n2]  (v*3+d)
   real* sOp = sQ + NE * 6 * 15 * n2;               // DhatT, lm, lp, lhm, lhp
   int* sES = reinterpret_cast<int*>(sOp + n2 + 4 * n);
-  float* sOut = reinterpret_cast<float*>(sES + ((NE * 6 + 3) & ~3));  // [NE][5][n3] (SW != 0)
 
   const int tid = threadIdx.x;
   const int el = tid / n3, node = tid - el * n3;
@@ -168,6 +201,7 @@ __global__ void __launch_bounds__(Cfg<n>::T) k_lift_vol(
   const int e = e0 + el;
   const bool valid = e < K;
   const int i = node % n, j = (node / n) % n, k = node / n2;
+  const int pn = pidx<n>(i, j, k);
 
   load_ops<real, n>(sOp, ops, tid, T);
   for (int t = tid; t < NE * 6; t += T) sES[t] = (e0 + t / 6 < K) ? elemSide[(size_t)e0 * 6 + t] : 0;
@@ -214,8 +248,7 @@ __global__ void __launch_bounds__(Cfg<n>::T) k_lift_vol(
   }
 
   real G[15];
-  real* myb = sbuf + el * 15 * n3;
-  const real* sD = sOp;
+  real* myb = sbuf + el * 15 * n3p;
   const real* lhm = sOp + n2 + 2 * n;
   const real* lhp = sOp + n2 + 3 * n;
   const real* Qe = sQ + el * 6 * 15 * n2;
@@ -227,18 +260,21 @@ __global__ void __launch_bounds__(Cfg<n>::T) k_lift_vol(
     for (int l = 0; l < 3; ++l) {
       const real a = jac[l * 3 + d];
 #pragma unroll
-      for (int v = 0; v < NV; ++v) myb[(l * NV + v) * n3 + node] = a * W[v];
+      for (int v = 0; v < NV; ++v) myb[(l * NV + v) * n3p + pn] = a * W[v];
     }
     __syncthreads();
     real acc[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) acc[v] = real(0);
-    if constexpr (SW == 0) {
-      dhat_sweep3<real, n>(sD, myb, i, j, k, acc);
+    if constexpr (SW == 0 && sizeof(real) == 8) {
+      node_sweep3<real, n>(sOp, myb, i, j, k, acc);
     } else {
-      tc_sweep3<n, NE, SW>(reinterpret_cast<const float*>(sbuf), sOut, bfr, tid, T);
+      if constexpr (SW == 0)
+        line_sweep3<real, n>(sbuf, sOut, ops, tid);
+      else
+        tc_sweep3<n, NE, SW>(reinterpret_cast<const float*>(sbuf), reinterpret_cast<float*>(sOut), bfr, tid, T);
 #pragma unroll
-      for (int v = 0; v < NV; ++v) acc[v] = sOut[(el * NV + v) * n3 + node];
+      for (int v = 0; v < NV; ++v) acc[v] = sOut[(el * NV + v) * n3p + pn];
     }
     const real c0 = lhm[i], c1 = lhp[i], c2 = lhm[j], c3 = lhp[j], c4 = lhm[k], c5 = lhp[k];
 #pragma unroll
@@ -254,7 +290,7 @@ __global__ void __launch_bounds__(Cfg<n>::T) k_lift_vol(
   // a4: gradients to the faces
   __syncthreads();
 #pragma unroll
-  for (int c = 0; c < 15; ++c) myb[c * n3 + node] = G[c];
+  for (int c = 0; c < 15; ++c) myb[c * n3p + pn] = G[c];
   if (Gvol != nullptr && valid) {
 #pragma unroll
     for (int c = 0; c < 15; ++c) Gvol[((size_t)e * 15 + c) * n3 + node] = G[c];
@@ -273,10 +309,10 @@ __global__ void __launch_bounds__(Cfg<n>::T) k_lift_vol(
       const int l = s >> 1;
       const real* lv = (s & 1) ? lp : lm;
       const int p = pq % n, q = pq / n;
-      const real* b = sbuf + (el2 * 15 + c) * n3;
+      const real* b = sbuf + (el2 * 15 + c) * n3p;
       real val = real(0);
 #pragma unroll
-      for (int a = 0; a < n; ++a) val += lv[a] * b[vol_index(l, a, p, q, n)];
+      for (int a = 0; a < n; ++a) val += lv[a] * b[pvol_index<n>(l, a, p, q)];
       const int es = sES[el2 * 6 + s];
       const int mpq = orient_pq(es_orient(es), n - 1, p, q);
       Gf[((size_t)(es_slave(es) * S + es_side(es)) * 15 + c) * n2 + mpq] = val;
@@ -294,7 +330,7 @@ __global__ void __launch_bounds__(Cfg<n>::T) k_lift_vol(
       const real a = jac[l * 3 + d];
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
-        real* dst = &myb[(l * NV + v) * n3 + node];
+        real* dst = &myb[(l * NV + v) * n3p + pn];
         *dst = (d == 0 ? real(0) : *dst) + a * F[v];
       }
     }
@@ -304,12 +340,15 @@ __global__ void __launch_bounds__(Cfg<n>::T) k_lift_vol(
   real acc[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) acc[v] = real(0);
-  if constexpr (SW == 0) {
-    dhat_sweep3<real, n>(sD, myb, i, j, k, acc);
+  if constexpr (SW == 0 && sizeof(real) == 8) {
+    node_sweep3<real, n>(sOp, myb, i, j, k, acc);
   } else {
-    tc_sweep3<n, NE, SW>(reinterpret_cast<const float*>(sbuf), sOut, bfr, tid, T);
+    if constexpr (SW == 0)
+      line_sweep3<real, n>(sbuf, sOut, ops, tid);
+    else
+      tc_sweep3<n, NE, SW>(reinterpret_cast<const float*>(sbuf), reinterpret_cast<float*>(sOut), bfr, tid, T);
 #pragma unroll
-    for (int v = 0; v < NV; ++v) acc[v] = sOut[(el * NV + v) * n3 + node];
+    for (int v = 0; v < NV; ++v) acc[v] = sOut[(el * NV + v) * n3p + pn];
   }
   if (valid) {
 #pragma unroll
@@ -320,8 +359,10 @@ __global__ void __launch_bounds__(Cfg<n>::T) k_lift_vol(
 template <typename real, int n, int SW>
 constexpr size_t lift_vol_smem() {
   using C = Cfg<n>;
-  return sizeof(real) * (C::NE * 15 * C::n3 + C::NE * 6 * 15 * C::n2 + C::n2 + 4 * n) +
-         sizeof(int) * ((C::NE * 6 + 3) & ~3) + (SW != 0 ? sizeof(float) * C::NE * NV * C::n3 : 0);
+  // the FP64 form sweeps per node and needs no result buffer
+  constexpr int out = (sizeof(real) == 8 && SW == 0) ? 0 : C::NE * NV * C::n3p;
+  return sizeof(real) * (C::NE * 15 * C::n3p + out + C::NE * 6 * 15 * C::n2 + C::n2 + 4 * n) +
+         sizeof(int) * C::NE * 6;
 }
 
 // ---------------------------------------------------------------------------

@@ -96,7 +96,7 @@ __device__ __forceinline__ BFrag<SW> make_bfrag(const float* sD, int lane) {
 template <int n, int NE, int SW>
 __device__ __forceinline__ void tc_sweep3(const float* __restrict__ buf, float* __restrict__ sOut,
                                           const BFrag<SW>& bf, int tid, int T) {
-  constexpr int n2 = n * n, n3 = n2 * n;
+  constexpr int n2 = n * n, n3p = Cfg<n>::n3p, P = Cfg<n>::P;
   constexpr int L = NE * NV * n2;  // lines per direction
   constexpr int tiles = (L + 15) / 16;
   const int warp = tid >> 5, lane = tid & 31;
@@ -117,10 +117,10 @@ __device__ __forceinline__ void tc_sweep3(const float* __restrict__ buf, float* 
           const int el = gg / (NV * n2);
           const int rem = gg - el * NV * n2;
           const int v = rem / n2, line = rem - v * n2;
-          fld[h] = (el * 15 + l * NV + v) * n3;
-          base[h] = l == 0 ? n * line : (l == 1 ? (line % n) + n2 * (line / n) : line);
+          fld[h] = (el * 15 + l * NV + v) * n3p;
+          base[h] = l == 0 ? P * line : (l == 1 ? (line % n) + P * n * (line / n) : (line % n) + P * (line / n));
         }
-        const int stride = l == 0 ? 1 : (l == 1 ? n : n2);
+        const int stride = l == 0 ? 1 : (l == 1 ? P : P * n);
         auto Aval = [&](int h, int a) -> float {
           return (ok[h] && a < n) ? buf[fld[h] + base[h] + stride * a] : 0.f;
         };
@@ -168,7 +168,7 @@ __device__ __forceinline__ void tc_sweep3(const float* __restrict__ buf, float* 
           const int el = g / (NV * n2);
           const int rem = g - el * NV * n2;
           const int v = rem / n2;
-          float* out = sOut + (el * NV + v) * n3 + base[h];
+          float* out = sOut + (el * NV + v) * n3p + base[h];
 #pragma unroll
           for (int cc = 0; cc < 2; ++cc) {
             const int i = 2 * tig + cc;
