@@ -135,6 +135,25 @@ flexi_status flexi_rk_run_host(flexi_ctx *ctx, void *U_host, int nsteps, double 
  * the status word was set (and clears it). */
 flexi_status flexi_reduce(flexi_ctx *ctx, const void *U, const void *Ut, double cfl, double *out, void *stream);
 
+/* Allocation-free form of flexi_reduce, for callers that cannot allocate
+ * device memory when they need the sums (an application whose own memory
+ * manager owns all device memory, or a time loop that must not call
+ * cudaMalloc/cudaFree because they synchronise the device).  It computes the
+ * same 8 outputs as flexi_reduce (same layout, same FLEXI_ENONPHYSICAL report)
+ * but keeps its per-element partial sums in a fixed array in the library's
+ * static device memory instead of a context buffer, and calls no allocating
+ * routine.  The paper has no counterpart of this call.
+ *   - Limit: K <= FLEXI_NOALLOC_MAX_ELEMENTS elements; larger meshes return
+ *     FLEXI_EINVAL.  The static array (about 4.5 MiB) is held by every GPU
+ *     that loads the library until the process exits.
+ *   - The first call on a device looks up the array's device address (once per
+ *     device); make that first call before any stream capture.
+ *   - All calls share the array: calls whose work overlaps on the GPU (several
+ *     streams or host threads on one device) race on it.  Synchronises `stream`. */
+#define FLEXI_NOALLOC_MAX_ELEMENTS 65536
+flexi_status flexi_reduce_noalloc(flexi_ctx *ctx, const void *U, const void *Ut, double cfl, double *out,
+                                  void *stream);
+
 enum {
   FLEXI_Q_K = 0, FLEXI_Q_N = 1, FLEXI_Q_NSIDES = 2, FLEXI_Q_NBCSIDES = 3, FLEXI_Q_DOF = 4,
   FLEXI_Q_BYTES_PER_STAGE = 5, /* algorithmic HBM bytes of one RK stage (minimum-traffic schedule) */

@@ -17,7 +17,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libflexi_gb300.so")
-SOURCES = ["flexi_api.cu", "k_geom.cu", "k_dg_f64.cu", "k_dg_f32.cu", "k_adj_f64.cu", "k_adj_f32.cu"]
+SOURCES = ["flexi_api.cu", "k_geom.cu", "k_dg_f64.cu", "k_dg_f32.cu", "k_adj_f64.cu", "k_adj_f32.cu",
+           "k_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -501,6 +501,22 @@ flexi_status do_reduce(flexi_ctx* c, const void* U, const void* Ut, double cfl, 
 }  // namespace
 
 namespace flexi {
+bool ctx_reduce_inputs(const flexi_ctx* c, ReduceInputs* r) {
+  if (c == nullptr || r == nullptr) return false;
+  r->K = c->K;
+  r->N = c->N;
+  r->n3 = c->n3;
+  r->fp64 = c->fp64 ? 1 : 0;
+  r->wJ = c->wJ;
+  r->Ja64 = c->Ja64;
+  r->sJ64 = c->sJ64;
+  r->status = c->status;
+  r->kv_coef = std::max(4.0 / 3.0, c->p.gamma / c->p.Pr) * c->p.mu;
+  r->ph64 = c->ph64;
+  r->ph32 = c->ph32;
+  return true;
+}
+
 size_t adjoint_scratch_bytes(const DevMesh& m, size_t rs) {
   const size_t n2 = (size_t)m.n * m.n, n3 = n2 * m.n;
   return rs * (4 * 2 * (size_t)m.S * NV * n2 + 2 * (size_t)m.S * 15 * n2 + (size_t)m.K * NV * n3);

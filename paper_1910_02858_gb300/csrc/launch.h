@@ -68,6 +68,21 @@ cudaError_t launch_reduce(const real* U, const real* Ut, const double* wJ, const
                           long long nodes, int n3, const Phys<real>& ph, double kv_coef, double* partial,
                           int nblocks, cudaStream_t st);
 constexpr int kReduceQuantities = 9;
+}  // namespace flexi
+struct flexi_ctx;
+namespace flexi {
+
+// read-only view of a context's inputs to the global reductions
+struct ReduceInputs {
+  int K = 0, N = 0, n3 = 0, fp64 = 1;
+  const double *wJ = nullptr, *Ja64 = nullptr, *sJ64 = nullptr;
+  const unsigned* status = nullptr;
+  double kv_coef = 0;  // max(4/3, gamma/Pr) mu
+  Phys<double> ph64{};
+  Phys<float> ph32{};
+};
+
+bool ctx_reduce_inputs(const flexi_ctx* c, ReduceInputs* r);
 
 // geometry (FP64)
 cudaError_t geom_apply1d(const double* in, double* out, const double* M, int B, int ni, int nj, int nk, int l,

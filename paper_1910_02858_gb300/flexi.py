@@ -24,8 +24,9 @@ KERNEL_CLASSES = ["lift_vol", "face", "surf_rk", "prolong", "bc", "adjoint", "re
 
 # every entry point declared in include/flexi.h
 EXPORTS = ["flexi_mesh_init", "flexi_rhs", "flexi_rk_step", "flexi_rk_step_stages", "flexi_adjoint_step",
-           "flexi_rhs_adjoint", "flexi_rk_run_host", "flexi_reduce", "flexi_query", "flexi_profile",
-           "flexi_kernel_times", "flexi_strerror", "flexi_destroy"]
+           "flexi_rhs_adjoint", "flexi_rk_run_host", "flexi_reduce", "flexi_reduce_noalloc", "flexi_query",
+           "flexi_profile", "flexi_kernel_times", "flexi_strerror", "flexi_destroy"]
+NOALLOC_MAX_ELEMENTS = 65536
 
 
 class flexi_params(ctypes.Structure):
@@ -61,6 +62,7 @@ def lib() -> ctypes.CDLL:
         L.flexi_rhs_adjoint.argtypes = [vp, vp, vp, vp, d, vp]
         L.flexi_rk_run_host.argtypes = [vp, vp, i, d, d, vp]
         L.flexi_reduce.argtypes = [vp, vp, vp, d, ctypes.POINTER(ctypes.c_double), vp]
+        L.flexi_reduce_noalloc.argtypes = [vp, vp, vp, d, ctypes.POINTER(ctypes.c_double), vp]
         L.flexi_query.argtypes = [vp, i, i64p]
         L.flexi_profile.argtypes = [vp, i]
         L.flexi_kernel_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double), i64p, i]
@@ -138,6 +140,14 @@ def flexi_reduce(ctx, U, Ut=None, cfl=0.9, stream=None, allow_nonphysical=False)
     code = lib().flexi_reduce(ctx, _ptr(U), _ptr(Ut), float(cfl), out, _stream(stream))
     if not (allow_nonphysical and code == FLEXI_ENONPHYSICAL):
         check(code, "flexi_reduce")
+    return list(out), code
+
+
+def flexi_reduce_noalloc(ctx, U, Ut=None, cfl=0.9, stream=None):
+    """Same outputs as flexi_reduce, without any device allocation (returns the
+    8 values and the status code, which is not raised)."""
+    out = (ctypes.c_double * 8)()
+    code = lib().flexi_reduce_noalloc(ctx, _ptr(U), _ptr(Ut), float(cfl), out, _stream(stream))
     return list(out), code
 
 
