@@ -288,11 +288,14 @@ def perturbed(x: np.ndarray, seed: int, amp: float = 0.05, Ma: float = 0.3, gamm
     return prim_to_cons_np(rho, u, v, w, p, gamma)
 
 
-def random_directions(shape, count: int, seed0: int = 1910) -> list[np.ndarray]:
-    """Seeded unit-L2 random directions (N(0,1) per entry, then normalised)."""
+def random_directions(shape, count: int, seed0: int = 1910, norm: str = "l2") -> list[np.ndarray]:
+    """Seeded random directions with N(0,1) entries (seed seed0 + i), scaled to
+    unit L2 norm (norm="l2") or to unit RMS per entry (norm="rms", i.e. left as
+    drawn up to the sample RMS)."""
     out = []
     for i in range(count):
         rng = np.random.default_rng(seed0 + i)
         v = rng.normal(size=shape)
-        out.append(v / np.linalg.norm(v))
+        scale = np.linalg.norm(v) if norm == "l2" else np.sqrt(np.mean(v * v))
+        out.append(v / scale)
     return out
