@@ -45,6 +45,24 @@ def peaks():
         return {}
 
 
+# DRAM bytes (read + write) per launch of k_lift_vol from the ncu captures
+# summarised in profiles/, keyed by form and by a hash of the kernel sources at
+# capture time; reported only while the sources are unchanged (else null).
+KERNEL_SOURCES = ["paper_1910_02858_gb300/csrc/k_dg.cuh", "paper_1910_02858_gb300/csrc/dg_common.cuh",
+                  "paper_1910_02858_gb300/csrc/k_tc.cuh"]
+NCU_TRAFFIC = {("fp64", "7061f27bc8f1228e"): 574002944, ("fp32", "7061f27bc8f1228e"): 266459392}
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 # GB300 FP64 FMA peak derived from unit counts and clocks: 152 SMs x 2 DFMA/clk
 # (4 FP64 flop/clk/SM, consistent with the nominal 1.25 TFLOP/s) x 2070 MHz.
 FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12
@@ -289,17 +307,18 @@ def main():
     lv_ms, lv_cnt = ktimes["lift_vol"]
     lv_avg_s = lv_ms / max(lv_cnt, 1) * 1e-3
     share = lv_ms / max(sum(v[0] for v in ktimes.values()), 1e-9)
+    traffic = NCU_TRAFFIC.get((args.form, kernel_source_hash()))
     if args.form == "fp64":
         achieved_tflops = flops_lv * dof / lv_avg_s / 1e12
         roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": achieved_tflops / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "k_lift_vol<double,8>",
+                    "frac": achieved_tflops / FP64_PEAK_TFLOPS, "traffic": traffic, "kernel": "k_lift_vol<double,8>",
                     "peak_source": "derived: 152 SM x 4 FP64 flop/clk x 2070 MHz (nominal 1.25 TFLOP/s)",
                     "kernel_share": share}
     else:
         hbm = peaks().get("hbm_gbs", 6800.0)
         achieved = bytes_lv * dof / lv_avg_s / 1e9
         roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                    "traffic": None, "kernel": f"k_lift_vol<float,8,{args.form}>",
+                    "traffic": traffic, "kernel": f"k_lift_vol<float,8,{args.form}>",
                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks() else "fallback 6.8 TB/s",
                     "kernel_share": share}
     step_bytes_gbs = bytes_stage * dof * NSTAGES / (ms_step * 1e-3) / 1e9

@@ -36,10 +36,14 @@ __device__ __forceinline__ void load_ops(real* s, const Ops<real>& ops, int tid,
 //   out[el][v][node] = sum_l sum_a Dhat[i_l][a] buf[el][l*5+v][node with index_l = a].
 // One thread per line: the line's n values are read once from shared memory and
 // D_hat comes from the kernel-parameter bank at compile-time offsets.  The three
-// directions accumulate into out one after the other.  Block-wide; ends synced.
+// directions accumulate into out one after the other.  With Q != nullptr (the
+// lifting of gradient component d) the two face terms of each line,
+// l_hat_i(-1) Q[-face] + l_hat_i(+1) Q[+face], are added in the same pass
+// (the face node of a line of direction l has (p, q) = the line's free indices).
+// Block-wide; ends synced.
 template <typename real, int n>
 __device__ __forceinline__ void line_sweep3(const real* __restrict__ buf, real* __restrict__ out,
-                                            const Ops<real>& ops, int tid) {
+                                            const real* __restrict__ Q, int d, const Ops<real>& ops, int tid) {
   using C = Cfg<n>;
   constexpr int n2 = C::n2, n3p = C::n3p, P = C::P, NE = C::NE, T = C::T;
   constexpr int L = NE * NV * n2;
@@ -56,10 +60,15 @@ __device__ __forceinline__ void line_sweep3(const real* __restrict__ buf, real* 
       real x[n];
 #pragma unroll
       for (int a = 0; a < n; ++a) x[a] = src[a * stride];
+      real qm = real(0), qp = real(0);
+      if (Q != nullptr) {
+        qm = Q[((el * 6 + 2 * l) * 15 + v * 3 + d) * n2 + line];
+        qp = Q[((el * 6 + 2 * l + 1) * 15 + v * 3 + d) * n2 + line];
+      }
       real* dst = out + (el * NV + v) * n3p + base;
 #pragma unroll
       for (int ii = 0; ii < n; ++ii) {
-        real y = real(0);
+        real y = ops.lhm[ii] * qm + ops.lhp[ii] * qp;
 #pragma unroll
         for (int a = 0; a < n; ++a) y += ops.DhatT[a * n + ii] * x[a];
         dst[ii * stride] = (l == 0) ? y : dst[ii * stride] + y;
@@ -266,25 +275,29 @@ __global__ void __launch_bounds__(Cfg<n>::T) k_lift_vol(
     real acc[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) acc[v] = real(0);
+    constexpr bool kLines = (SW == 0 && sizeof(real) == 4);  // FP32: line sweeps with the face terms folded in
     if constexpr (SW == 0 && sizeof(real) == 8) {
       node_sweep3<real, n>(sOp, myb, i, j, k, acc);
     } else {
       if constexpr (SW == 0)
-        line_sweep3<real, n>(sbuf, sOut, ops, tid);
+        line_sweep3<real, n>(sbuf, sOut, sQ, d, ops, tid);
       else
         tc_sweep3<n, NE, SW>(reinterpret_cast<const float*>(sbuf), reinterpret_cast<float*>(sOut), bfr, tid, T);
 #pragma unroll
       for (int v = 0; v < NV; ++v) acc[v] = sOut[(el * NV + v) * n3p + pn];
     }
-    const real c0 = lhm[i], c1 = lhp[i], c2 = lhm[j], c3 = lhp[j], c4 = lhm[k], c5 = lhp[k];
+    if constexpr (!kLines) {
+      const real c0 = lhm[i], c1 = lhp[i], c2 = lhm[j], c3 = lhp[j], c4 = lhm[k], c5 = lhp[k];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      const int o = (v * 3 + d) * n2;
-      acc[v] += c0 * Qe[0 * 15 * n2 + o + pq0] + c1 * Qe[1 * 15 * n2 + o + pq0];
-      acc[v] += c2 * Qe[2 * 15 * n2 + o + pq1] + c3 * Qe[3 * 15 * n2 + o + pq1];
-      acc[v] += c4 * Qe[4 * 15 * n2 + o + pq2] + c5 * Qe[5 * 15 * n2 + o + pq2];
-      G[d * NV + v] = acc[v] * sj;
+      for (int v = 0; v < NV; ++v) {
+        const int o = (v * 3 + d) * n2;
+        acc[v] += c0 * Qe[0 * 15 * n2 + o + pq0] + c1 * Qe[1 * 15 * n2 + o + pq0];
+        acc[v] += c2 * Qe[2 * 15 * n2 + o + pq1] + c3 * Qe[3 * 15 * n2 + o + pq1];
+        acc[v] += c4 * Qe[4 * 15 * n2 + o + pq2] + c5 * Qe[5 * 15 * n2 + o + pq2];
+      }
     }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) G[d * NV + v] = acc[v] * sj;
   }
 
   // a4: gradients to the faces
@@ -297,41 +310,61 @@ __global__ void __launch_bounds__(Cfg<n>::T) k_lift_vol(
   }
   __syncthreads();
   {
-    const real* lm = sOp + n2;
-    const real* lp = sOp + n2 + n;
-    for (int it = tid; it < NE * 6 * 15 * n2; it += T) {
-      const int el2 = it / (6 * 15 * n2);
-      int r = it - el2 * 6 * 15 * n2;
-      const int s = r / (15 * n2);
-      r -= s * 15 * n2;
-      const int c = r / n2, pq = r - c * n2;
+    // one pass per line of direction l gives the values on both faces -l and +l;
+    // the face node of the line has (p, q) = its free indices
+    constexpr int P = C::P;
+    for (int it = tid; it < NE * 3 * 15 * n2; it += T) {
+      const int el2 = it / (3 * 15 * n2);
+      int r = it - el2 * 3 * 15 * n2;
+      const int l = r / (15 * n2);
+      r -= l * 15 * n2;
+      const int c = r / n2, line = r - c * n2;
       if (e0 + el2 >= K) continue;
-      const int l = s >> 1;
-      const real* lv = (s & 1) ? lp : lm;
-      const int p = pq % n, q = pq / n;
-      const real* b = sbuf + (el2 * 15 + c) * n3p;
-      real val = real(0);
+      const int p = line % n, q = line / n;
+      const int stride = l == 0 ? 1 : (l == 1 ? P : P * n);
+      const int base = l == 0 ? P * line : (l == 1 ? p + P * n * q : p + P * q);
+      const real* b = sbuf + (el2 * 15 + c) * n3p + base;
+      real gm = real(0), gp = real(0);
 #pragma unroll
-      for (int a = 0; a < n; ++a) val += lv[a] * b[pvol_index<n>(l, a, p, q)];
-      const int es = sES[el2 * 6 + s];
-      const int mpq = orient_pq(es_orient(es), n - 1, p, q);
-      Gf[((size_t)(es_slave(es) * S + es_side(es)) * 15 + c) * n2 + mpq] = val;
+      for (int a = 0; a < n; ++a) {
+        const real x = b[a * stride];
+        gm += ops.lm[a] * x;
+        gp += ops.lp[a] * x;
+      }
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int es = sES[el2 * 6 + 2 * l + h];
+        const int mpq = orient_pq(es_orient(es), n - 1, p, q);
+        Gf[((size_t)(es_slave(es) * S + es_side(es)) * 15 + c) * n2 + mpq] = h ? gp : gm;
+      }
     }
   }
   __syncthreads();
 
-  // a6: contravariant fluxes Fcal^l = sum_d Ja^l_d (F^c_d - F^v_d), accumulated in shared memory
+  // a6: contravariant fluxes Fcal^l = sum_d Ja^l_d (F^c_d - F^v_d): in registers for
+  // FP32, accumulated in shared memory for FP64 (register budget)
+  if constexpr (sizeof(real) == 4) {
+    real F[3][NV];
 #pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    real F[NV];
-    flux_total(Uo, W, G, d, ph, F);
+    for (int d = 0; d < 3; ++d) flux_total(Uo, W, G, d, ph, F[d]);
 #pragma unroll
-    for (int l = 0; l < 3; ++l) {
-      const real a = jac[l * 3 + d];
+    for (int l = 0; l < 3; ++l)
 #pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        real* dst = &myb[(l * NV + v) * n3p + pn];
-        *dst = (d == 0 ? real(0) : *dst) + a * F[v];
+      for (int v = 0; v < NV; ++v)
+        myb[(l * NV + v) * n3p + pn] = jac[l * 3 + 0] * F[0][v] + jac[l * 3 + 1] * F[1][v] + jac[l * 3 + 2] * F[2][v];
+  } else {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      real F[NV];
+      flux_total(Uo, W, G, d, ph, F);
+#pragma unroll
+      for (int l = 0; l < 3; ++l) {
+        const real a = jac[l * 3 + d];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          real* dst = &myb[(l * NV + v) * n3p + pn];
+          *dst = (d == 0 ? real(0) : *dst) + a * F[v];
+        }
       }
     }
   }
@@ -344,7 +377,7 @@ __global__ void __launch_bounds__(Cfg<n>::T) k_lift_vol(
     node_sweep3<real, n>(sOp, myb, i, j, k, acc);
   } else {
     if constexpr (SW == 0)
-      line_sweep3<real, n>(sbuf, sOut, ops, tid);
+      line_sweep3<real, n>(sbuf, sOut, nullptr, 0, ops, tid);
     else
       tc_sweep3<n, NE, SW>(reinterpret_cast<const float*>(sbuf), reinterpret_cast<float*>(sOut), bfr, tid, T);
 #pragma unroll
