@@ -123,6 +123,22 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(value: float, dist=None, device=None) -> float:
+    """Slowest rank's time (the job is as slow as its slowest replica)."""
+    if dist is None:
+        return value
+    import torch
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_pid(seconds: float, steps: int, dof_per_rank: int, world: int) -> float:
+    """PID of the whole job in ns per DOF per RK stage: wall / (all ranks' DOF * steps * stages)."""
+    return seconds * 1e9 / (steps * NSTAGES * dof_per_rank * world)
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -292,12 +308,9 @@ def main():
     ms_total = ev0.elapsed_time(ev1)
     ktimes = F.flexi_kernel_times(s.ctx, reset=True)
     F.flexi_profile(s.ctx, False)
-    if dist is not None:
-        tt = torch.tensor([ms_total], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms_total = float(tt.item())
+    ms_total = max_over_ranks(ms_total, dist, dev)
     ms_step = ms_total / args.steps
-    pid = ms_total * 1e6 / (args.steps * NSTAGES * dof * world)  # whole job
+    pid = whole_job_pid(ms_total * 1e-3, args.steps, dof, world)
 
     # roofline of the dominant kernel (lifting + volume): FP64 form ALU-bound (FP64 pipe),
     # FP32 forms HBM-bound
@@ -333,11 +346,8 @@ def main():
         F.flexi_rk_run_host(s.ctx, Uh, 1, k * dt, dt, stream)
     e2e_s = time.perf_counter() - t0
     e2e_steps = max(3, args.steps // 2)
-    if dist is not None:
-        tt = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt.item())
-    e2e_pid = e2e_s * 1e9 / (e2e_steps * NSTAGES * dof * world)
+    e2e_s = max_over_ranks(e2e_s, dist, dev)
+    e2e_pid = whole_job_pid(e2e_s, e2e_steps, dof, world)
     ubytes = U.numel() * U.element_size()
 
     line = {"metric": METRIC, "value": pid, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -421,10 +431,38 @@ def extras(args, s64, U0, mesh, dt, dev, F, wl, Solver, SolverConfig, torch, np)
         finally:
             s.close()
     try:
+        out["lobatto"] = lobatto_pid(mesh, dt, dev, F, wl, Solver, SolverConfig, torch)
+    except Exception as exc:
+        out["lobatto"] = {"error": repr(exc)}
+    try:
         out["adjoint"] = adjoint_ratio(dev, F, wl, Solver, SolverConfig, torch)
     except Exception as exc:
         out["adjoint"] = {"error": repr(exc)}
     return out
+
+
+def lobatto_pid(mesh, dt, dev, F, wl, Solver, SolverConfig, torch):
+    """The same 16^3, N = 7 Taylor-Green step on Gauss-Lobatto nodes (prolongation
+    is a copy, face terms touch only face nodes), FP64 and FP32."""
+    res = {}
+    x = mesh.node_coords(7, 1)
+    for name, prec in (("fp64", F.FP64), ("fp32", F.FP32)):
+        s = Solver(SolverConfig(N=7, node_type=F.NODES_LOBATTO, riemann=F.RIEMANN_HLLC, precision=prec),
+                   mesh.coords, mesh.conn, device=dev)
+        U = torch.tensor(wl.taylor_green(x), device=dev, dtype=s.dtype)
+        dU = torch.zeros_like(U)
+        for _ in range(3):
+            s.step(U, dU, 0.0, dt)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for k in range(10):
+            s.step(U, dU, k * dt, dt)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        res[name] = {"pid": e0.elapsed_time(e1) * 1e6 / (10 * NSTAGES * s.query(F.Q_DOF)), "steps": 10}
+        s.close()
+    return res
 
 
 def adjoint_ratio(dev, F, wl, Solver, SolverConfig, torch):

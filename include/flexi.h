@@ -54,9 +54,10 @@ typedef enum {
 } flexi_status;
 
 enum { FLEXI_NODES_GAUSS = 0, FLEXI_NODES_LOBATTO = 1 };
-/* Riemann solvers (Sec. 2.2 names Roe and HLL-type fluxes): ROE_SMOOTH replaces
- * |lambda| by (lambda^2 + delta^2)/(2 delta) below delta = 0.1 c (C^1 operator). */
-enum { FLEXI_RIEMANN_ROE = 0, FLEXI_RIEMANN_HLLC = 1, FLEXI_RIEMANN_ROE_SMOOTH = 2 };
+/* Riemann solvers (Sec. 2.2 names Roe, HLL-type and Rusanov fluxes): ROE_SMOOTH
+ * replaces |lambda| by (lambda^2 + delta^2)/(2 delta) below delta = 0.1 c (C^1
+ * operator); RUSANOV is the local Lax-Friedrichs flux. */
+enum { FLEXI_RIEMANN_ROE = 0, FLEXI_RIEMANN_HLLC = 1, FLEXI_RIEMANN_ROE_SMOOTH = 2, FLEXI_RIEMANN_RUSANOV = 3 };
 /* Arithmetic forms: FP64; FP32 storage+flux math with FP32 line sweeps; FP32
  * with the D-matrix line sweeps on tensor cores in TF32 or BF16, each operand
  * split into three terms of the narrow type (six products, FP32 accumulation). */
@@ -113,7 +114,8 @@ flexi_status flexi_rk_step_stages(flexi_ctx *ctx, void *U, void *dU, double t, d
  *                 lam_dU = A_k lam_dU.
  * U_stages: device [5][K][5][n^3] as written by flexi_rk_step_stages;
  * lamU, lam_dU: device, updated in place.  Requires FLEXI_FP64 or FLEXI_FP32
- * and a Roe-type flux; periodic meshes only (FLEXI_EUNSUPPORTED otherwise). */
+ * and a Roe-type flux (ROE or ROE_SMOOTH); periodic meshes without source term
+ * only (FLEXI_EUNSUPPORTED otherwise). */
 flexi_status flexi_adjoint_step(flexi_ctx *ctx, const void *U_stages, void *lamU, void *lam_dU, double t,
                                 double dt, void *stream);
 

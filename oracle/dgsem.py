@@ -57,7 +57,7 @@ RK_C = [0.0,
         2006345519317.0 / 3224310063776.0,
         2802321613138.0 / 2924317926251.0]
 
-ROE, HLLC = 0, 1
+ROE, HLLC, RUSANOV = 0, 1, 3
 
 
 @dataclass
@@ -86,6 +86,8 @@ class DGSEM:
     def _riemann(self, UL, UR, nv):
         if self.p.riemann == ROE:
             return eq.riemann_roe(UL, UR, nv, self.gas, smooth=self.p.smooth_roe)
+        if self.p.riemann == RUSANOV:
+            return eq.riemann_rusanov(UL, UR, nv, self.gas)
         return eq.riemann_hllc(UL, UR, nv, self.gas)
 
     def rhs(self, U: torch.Tensor, t: float = 0.0, parts: bool = False):

@@ -17,6 +17,8 @@ Sec. 2.2) without formulas.  Readings, all standard ideal-gas forms:
   (makes the discrete operator C^1 for finite-difference checks of the adjoint).
 * HLLC (Toro): S_L = min(u_nL - c_L, u_roe - c_roe), S_R = max(u_nR + c_R,
   u_roe + c_roe), contact speed from the jump conditions, 4-branch star flux.
+* Rusanov (local Lax-Friedrichs): (F_L + F_R).n / 2 - lambda_max (U_R - U_L) / 2,
+  lambda_max = max(|u_nL| + c_L, |u_nR| + c_R).
 
 Variables are in the LAST tensor dimension (length 5); gradients are
 ``[..., 3 (x_d), 5 (var)]``; normals ``[..., 3]``.
@@ -131,6 +133,18 @@ def riemann_roe(UL, UR, n, gas, smooth: bool = False):
     diss = (l1 * a1).unsqueeze(-1) * r1 + (l5 * a5).unsqueeze(-1) * r5 + (l2 * a2).unsqueeze(-1) * r2 \
         + (l2 * rho).unsqueeze(-1) * rt
     return 0.5 * (FL + FR) - 0.5 * diss
+
+
+def riemann_rusanov(UL, UR, n, gas):
+    """Rusanov / local Lax-Friedrichs flux."""
+    WL, WR = prim(UL, gas), prim(UR, gas)
+    FL, FR = _euler_normal_flux(UL, WL, n), _euler_normal_flux(UR, WR, n)
+    cL = torch.sqrt(gas.gamma * WL[..., 4] / WL[..., 0])
+    cR = torch.sqrt(gas.gamma * WR[..., 4] / WR[..., 0])
+    uL = (WL[..., 1:4] * n).sum(-1)
+    uR = (WR[..., 1:4] * n).sum(-1)
+    lam = torch.maximum(torch.abs(uL) + cL, torch.abs(uR) + cR)
+    return 0.5 * (FL + FR) - 0.5 * lam.unsqueeze(-1) * (UR - UL)
 
 
 def riemann_hllc(UL, UR, n, gas):

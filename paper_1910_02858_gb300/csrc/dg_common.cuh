@@ -275,11 +275,34 @@ __device__ __forceinline__ void riemann_roe(const real WL[NV], const real WR[NV]
   f[4] = real(0.5) * (FL[4] + FR[4] - (w1 * (H - un * c) + w5 * (H + un * c) + w2 * real(0.5) * q2 + wt * vdvt));
 }
 
+// Rusanov (local Lax-Friedrichs): central flux minus lambda_max/2 times the jump
+template <typename real>
+__device__ __forceinline__ void riemann_rusanov(const real WL[NV], const real WR[NV], const real n[3],
+                                                const Phys<real>& ph, real f[NV]) {
+  const real q2L = WL[1] * WL[1] + WL[2] * WL[2] + WL[3] * WL[3];
+  const real q2R = WR[1] * WR[1] + WR[2] * WR[2] + WR[3] * WR[3];
+  const real EL = WL[4] * ph.inv_gm1 + real(0.5) * WL[0] * q2L;
+  const real ER = WR[4] * ph.inv_gm1 + real(0.5) * WR[0] * q2R;
+  const real uL = WL[1] * n[0] + WL[2] * n[1] + WL[3] * n[2];
+  const real uR = WR[1] * n[0] + WR[2] * n[1] + WR[3] * n[2];
+  real FL[NV], FR[NV], UL[NV], UR[NV];
+  euler_normal(WL, EL, uL, n, FL);
+  euler_normal(WR, ER, uR, n, FR);
+  prim_to_cons(WL, UL, ph);
+  prim_to_cons(WR, UR, ph);
+  const real cL = dg_sqrt(ph.gamma * WL[4] / WL[0]), cR = dg_sqrt(ph.gamma * WR[4] / WR[0]);
+  const real lam = fmax(dg_abs(uL) + cL, dg_abs(uR) + cR);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) f[v] = real(0.5) * (FL[v] + FR[v]) - real(0.5) * lam * (UR[v] - UL[v]);
+}
+
 template <typename real>
 __device__ __forceinline__ void riemann(const real WL[NV], const real WR[NV], const real n[3],
                                         const Phys<real>& ph, real f[NV]) {
   if (ph.riemann == 1)
     riemann_hllc(WL, WR, n, ph, f);
+  else if (ph.riemann == 3)
+    riemann_rusanov(WL, WR, n, ph, f);
   else
     riemann_roe(WL, WR, n, ph, ph.riemann == 2, f);
 }

@@ -411,6 +411,7 @@ flexi_status mesh_init_impl(flexi_ctx* c, const flexi_params* p, int K, const do
   c->m.xsol = c->xsol;
   c->m.status = c->status;
   c->m.sweep_mode = p->precision == FLEXI_FP32_TF32 ? 1 : (p->precision == FLEXI_FP32_BF16 ? 2 : 0);
+  c->m.lgl = p->node_type == FLEXI_NODES_LOBATTO ? 1 : 0;
   const size_t rs = c->rs;
   if (c->fp64) {
     c->m.Ja = c->Ja64; c->m.sJ = c->sJ64; c->m.fgeo = c->fgeo64;
@@ -561,7 +562,7 @@ flexi_status flexi_mesh_init(flexi_ctx** out, const flexi_params* p, int K, cons
   if (p->N < 1 || p->N > 7) return p->N > 7 ? FLEXI_EUNSUPPORTED : FLEXI_EINVAL;
   if (p->Ngeo < 1 || p->Ngeo > p->N) return FLEXI_EINVAL;
   if (p->node_type != FLEXI_NODES_GAUSS && p->node_type != FLEXI_NODES_LOBATTO) return FLEXI_EINVAL;
-  if (p->riemann < 0 || p->riemann > 2 || p->bc_exact < 0 || p->bc_exact > 2) return FLEXI_EINVAL;
+  if (p->riemann < 0 || p->riemann > 3 || p->bc_exact < 0 || p->bc_exact > 2) return FLEXI_EINVAL;
   if (p->precision < FLEXI_FP64 || p->precision > FLEXI_FP32_BF16) return FLEXI_EINVAL;
   if (!(p->gamma > 1.0) || !(p->Pr > 0.0) || !(p->mu >= 0.0)) return FLEXI_EINVAL;
   if ((long long)K * 6 >= (1LL << 27)) return FLEXI_EUNSUPPORTED;
@@ -599,7 +600,8 @@ flexi_status flexi_rk_step_stages(flexi_ctx* c, void* U, void* dU, double t, dou
 }
 
 static bool adjoint_supported(const flexi_ctx* c) {
-  return c->nBC == 0 && c->p.riemann != FLEXI_RIEMANN_HLLC && !c->p.source;
+  return c->nBC == 0 && (c->p.riemann == FLEXI_RIEMANN_ROE || c->p.riemann == FLEXI_RIEMANN_ROE_SMOOTH) &&
+         !c->p.source;
 }
 
 flexi_status flexi_adjoint_step(flexi_ctx* c, const void* U_stages, void* lamU, void* lam_dU, double t, double dt,

@@ -41,7 +41,7 @@ __device__ __forceinline__ void load_ops(real* s, const Ops<real>& ops, int tid,
 // l_hat_i(-1) Q[-face] + l_hat_i(+1) Q[+face], are added in the same pass
 // (the face node of a line of direction l has (p, q) = the line's free indices).
 // Block-wide; ends synced.
-template <typename real, int n>
+template <typename real, int n, bool LGL>
 __device__ __forceinline__ void line_sweep3(const real* __restrict__ buf, real* __restrict__ out,
                                             const real* __restrict__ Q, int d, const Ops<real>& ops, int tid) {
   using C = Cfg<n>;
@@ -68,7 +68,9 @@ __device__ __forceinline__ void line_sweep3(const real* __restrict__ buf, real* 
       real* dst = out + (el * NV + v) * n3p + base;
 #pragma unroll
       for (int ii = 0; ii < n; ++ii) {
-        real y = ops.lhm[ii] * qm + ops.lhp[ii] * qp;
+        // on Gauss-Lobatto nodes l_hat(-1) / l_hat(+1) vanish except at the line's ends
+        real y = LGL ? (ii == 0 ? ops.lhm[0] * qm : (ii == n - 1 ? ops.lhp[n - 1] * qp : real(0)))
+                     : ops.lhm[ii] * qm + ops.lhp[ii] * qp;
 #pragma unroll
         for (int a = 0; a < n; ++a) y += ops.DhatT[a * n + ii] * x[a];
         dst[ii * stride] = (l == 0) ? y : dst[ii * stride] + y;
@@ -99,68 +101,115 @@ __device__ __forceinline__ void node_sweep3(const real* __restrict__ sD, const r
   }
 }
 
-// Face states of U (staged in shared memory as sU[el][5][n3]) for all six
-// faces of every element of the CTA: W(U_face) written to the side arrays.
-template <typename real, int n>
-__device__ __forceinline__ void faces_from_volume(const real* __restrict__ sU, const real* __restrict__ sOp,
+// Face states of U for all six faces of every element of the CTA, from U staged
+// in shared memory with padded lines (sU[el][5][n3p]): one pass per line of
+// direction l gives the values on both faces -l and +l (the face node of the
+// line has (p, q) = its free indices); W(U_face) goes to the side arrays.
+template <typename real, int n, bool LGL>
+__device__ __forceinline__ void faces_from_volume(const real* __restrict__ sU, const Ops<real>& ops,
                                                   const int* __restrict__ sES, int e0, int K, int S,
                                                   real* __restrict__ Wf, const Phys<real>& ph,
                                                   unsigned* __restrict__ status, int tid) {
   using C = Cfg<n>;
-  constexpr int n2 = C::n2, n3 = C::n3;
-  const real* lm = sOp + n2;
-  const real* lp = sOp + n2 + n;
-  for (int it = tid; it < C::NE * 6 * n2; it += C::T) {
-    const int el = it / (6 * n2);
-    const int r = it - el * 6 * n2;
-    const int s = r / n2, pq = r - s * n2;
-    const int e = e0 + el;
-    if (e >= K) continue;
-    const int l = s >> 1;
-    const real* lv = (s & 1) ? lp : lm;
-    const int p = pq % n, q = pq / n;
-    real Uf[NV];
+  constexpr int n2 = C::n2, n3p = C::n3p, P = C::P;
+  if constexpr (sizeof(real) == 8) {
+    // FP64 (FP64-pipe bound): one thread per face node keeps more warps on the pipe
+    for (int it = tid; it < C::NE * 6 * n2; it += C::T) {
+      const int el = it / (6 * n2);
+      const int r = it - el * 6 * n2;
+      const int s = r / n2, pq = r - s * n2;
+      if (e0 + el >= K) continue;
+      const int l = s >> 1, p = pq % n, q = pq / n;
+      real Uf[NV];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) Uf[v] = real(0);
+      for (int v = 0; v < NV; ++v) Uf[v] = real(0);
+      if (LGL) {  // the face node is a volume node: a copy
+        const int vi = pvol_index<n>(l, (s & 1) ? n - 1 : 0, p, q);
 #pragma unroll
-    for (int a = 0; a < n; ++a) {
-      const real c = lv[a];
-      const int vi = vol_index(l, a, p, q, n);
+        for (int v = 0; v < NV; ++v) Uf[v] = sU[(el * NV + v) * n3p + vi];
+      } else {
 #pragma unroll
-      for (int v = 0; v < NV; ++v) Uf[v] += c * sU[(el * NV + v) * n3 + vi];
+        for (int a = 0; a < n; ++a) {
+          const real c = (s & 1) ? ops.lp[a] : ops.lm[a];
+          const int vi = pvol_index<n>(l, a, p, q);
+#pragma unroll
+          for (int v = 0; v < NV; ++v) Uf[v] += c * sU[(el * NV + v) * n3p + vi];
+        }
+      }
+      real W[NV];
+      cons_to_prim(Uf, W, ph);
+      if (!(W[0] > real(0)) || !(W[4] > real(0))) atomicOr(status, 1u);
+      const int es = sES[el * 6 + s];
+      const int mpq = orient_pq(es_orient(es), n - 1, p, q);
+      real* dst = Wf + ((size_t)(es_slave(es) * S + es_side(es)) * NV) * n2 + mpq;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) dst[v * n2] = W[v];
     }
-    real W[NV];
-    cons_to_prim(Uf, W, ph);
-    if (!(W[0] > real(0)) || !(W[4] > real(0))) atomicOr(status, 1u);
-    const int es = sES[el * 6 + s];
-    const int side = es_side(es), slot = es_slave(es);
-    const int mpq = orient_pq(es_orient(es), n - 1, p, q);
-    real* dst = Wf + ((size_t)(slot * S + side) * NV) * n2 + mpq;
+    return;
+  }
+  for (int it = tid; it < C::NE * 3 * n2; it += C::T) {
+    const int el = it / (3 * n2);
+    const int r = it - el * 3 * n2;
+    const int l = r / n2, line = r - l * n2;
+    if (e0 + el >= K) continue;
+    const int p = line % n, q = line / n;
+    const int stride = l == 0 ? 1 : (l == 1 ? P : P * n);
+    const int base = l == 0 ? P * line : (l == 1 ? p + P * n * q : p + P * q);
+    real Um[NV], Up[NV];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) dst[v * n2] = W[v];
+    for (int v = 0; v < NV; ++v) Um[v] = Up[v] = real(0);
+    if (LGL) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        Um[v] = sU[(el * NV + v) * n3p + base];
+        Up[v] = sU[(el * NV + v) * n3p + base + (n - 1) * stride];
+      }
+    } else {
+#pragma unroll
+      for (int a = 0; a < n; ++a) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          const real x = sU[(el * NV + v) * n3p + base + a * stride];
+          Um[v] += ops.lm[a] * x;
+          Up[v] += ops.lp[a] * x;
+        }
+      }
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      real W[NV];
+      cons_to_prim(h ? Up : Um, W, ph);
+      if (!(W[0] > real(0)) || !(W[4] > real(0))) atomicOr(status, 1u);
+      const int es = sES[el * 6 + 2 * l + h];
+      const int mpq = orient_pq(es_orient(es), n - 1, p, q);
+      real* dst = Wf + ((size_t)(es_slave(es) * S + es_side(es)) * NV) * n2 + mpq;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) dst[v * n2] = W[v];
+    }
   }
 }
 
 // ---------------------------------------------------------------------------
 // a1: prolongation of U to the faces (primitive face states)
 // ---------------------------------------------------------------------------
-template <typename real, int n>
+template <typename real, int n, bool LGL>
 __global__ void __launch_bounds__(Cfg<n>::T) k_prolong(const real* __restrict__ U, const int* __restrict__ elemSide,
                                                         real* __restrict__ Wf, int K, int S, Ops<real> ops,
                                                         Phys<real> ph, unsigned* __restrict__ status) {
   using C = Cfg<n>;
-  constexpr int n3 = C::n3;
-  __shared__ real sU[C::NE * NV * n3];
-  __shared__ real sOp[n * n + 4 * n];
+  constexpr int n3 = C::n3, n3p = C::n3p;
+  __shared__ real sU[C::NE * NV * n3p];
   __shared__ int sES[C::NE * 6];
   const int tid = threadIdx.x;
   const int e0 = blockIdx.x * C::NE;
-  load_ops<real, n>(sOp, ops, tid, C::T);
   for (int t = tid; t < C::NE * 6; t += C::T) sES[t] = (e0 + t / 6 < K) ? elemSide[(size_t)e0 * 6 + t] : 0;
-  for (int t = tid; t < C::NE * NV * n3; t += C::T)
-    sU[t] = (e0 + t / (NV * n3) < K) ? U[(size_t)e0 * NV * n3 + t] : real(1);
+  for (int t = tid; t < C::NE * NV * n3; t += C::T) {
+    const int f = t / n3, node = t - f * n3;  // f = el * NV + v
+    sU[f * n3p + pidx<n>(node % n, (node / n) % n, node / (n * n))] =
+        (e0 + f / NV < K) ? U[(size_t)e0 * NV * n3 + t] : real(1);
+  }
   __syncthreads();
-  faces_from_volume<real, n>(sU, sOp, sES, e0, K, S, Wf, ph, status, tid);
+  faces_from_volume<real, n, LGL>(sU, ops, sES, e0, K, S, Wf, ph, status, tid);
 }
 
 // ---------------------------------------------------------------------------
@@ -188,7 +237,7 @@ __global__ void k_bc(const double* __restrict__ xbc, real* __restrict__ Wf, int 
 // a2-a4, a6, a7: lifting, gradient prolongation, volume integral
 // ---------------------------------------------------------------------------
 // SW: 0 line sweeps on the FP32/FP64 pipes; 1 TF32 and 2 BF16 3-term split mma (float only)
-template <typename real, int n, int SW>
+template <typename real, int n, int SW, bool LGL>
 __global__ void __launch_bounds__(Cfg<n>::T) k_lift_vol(
     const real* __restrict__ U, const real* __restrict__ Ja, const real* __restrict__ sJ,
     const real* __restrict__ Wf, const real* __restrict__ fgeo, const int* __restrict__ elemSide,
@@ -280,13 +329,13 @@ __global__ void __launch_bounds__(Cfg<n>::T) k_lift_vol(
       node_sweep3<real, n>(sOp, myb, i, j, k, acc);
     } else {
       if constexpr (SW == 0)
-        line_sweep3<real, n>(sbuf, sOut, sQ, d, ops, tid);
+        line_sweep3<real, n, LGL>(sbuf, sOut, sQ, d, ops, tid);
       else
         tc_sweep3<n, NE, SW>(reinterpret_cast<const float*>(sbuf), reinterpret_cast<float*>(sOut), bfr, tid, T);
 #pragma unroll
       for (int v = 0; v < NV; ++v) acc[v] = sOut[(el * NV + v) * n3p + pn];
     }
-    if constexpr (!kLines) {
+    if constexpr (!kLines && !LGL) {
       const real c0 = lhm[i], c1 = lhp[i], c2 = lhm[j], c3 = lhp[j], c4 = lhm[k], c5 = lhp[k];
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
@@ -294,6 +343,17 @@ __global__ void __launch_bounds__(Cfg<n>::T) k_lift_vol(
         acc[v] += c0 * Qe[0 * 15 * n2 + o + pq0] + c1 * Qe[1 * 15 * n2 + o + pq0];
         acc[v] += c2 * Qe[2 * 15 * n2 + o + pq1] + c3 * Qe[3 * 15 * n2 + o + pq1];
         acc[v] += c4 * Qe[4 * 15 * n2 + o + pq2] + c5 * Qe[5 * 15 * n2 + o + pq2];
+      }
+    } else if constexpr (!kLines) {  // Gauss-Lobatto: only nodes on a face receive its term
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const int o = (v * 3 + d) * n2;
+        if (i == 0) acc[v] += lhm[0] * Qe[0 * 15 * n2 + o + pq0];
+        if (i == n - 1) acc[v] += lhp[n - 1] * Qe[1 * 15 * n2 + o + pq0];
+        if (j == 0) acc[v] += lhm[0] * Qe[2 * 15 * n2 + o + pq1];
+        if (j == n - 1) acc[v] += lhp[n - 1] * Qe[3 * 15 * n2 + o + pq1];
+        if (k == 0) acc[v] += lhm[0] * Qe[4 * 15 * n2 + o + pq2];
+        if (k == n - 1) acc[v] += lhp[n - 1] * Qe[5 * 15 * n2 + o + pq2];
       }
     }
 #pragma unroll
@@ -309,7 +369,29 @@ __global__ void __launch_bounds__(Cfg<n>::T) k_lift_vol(
     for (int c = 0; c < 15; ++c) Gvol[((size_t)e * 15 + c) * n3 + node] = G[c];
   }
   __syncthreads();
-  {
+  if constexpr (sizeof(real) == 8) {
+    // FP64: one thread per (face node, component), more warps on the FP64 pipe
+    for (int it = tid; it < NE * 6 * 15 * n2; it += T) {
+      const int el2 = it / (6 * 15 * n2);
+      int r = it - el2 * 6 * 15 * n2;
+      const int s = r / (15 * n2);
+      r -= s * 15 * n2;
+      const int c = r / n2, pq = r - c * n2;
+      if (e0 + el2 >= K) continue;
+      const int l = s >> 1, p = pq % n, q = pq / n;
+      const real* b = sbuf + (el2 * 15 + c) * n3p;
+      real val = real(0);
+      if (LGL) {
+        val = b[pvol_index<n>(l, (s & 1) ? n - 1 : 0, p, q)];
+      } else {
+#pragma unroll
+        for (int a = 0; a < n; ++a) val += ((s & 1) ? ops.lp[a] : ops.lm[a]) * b[pvol_index<n>(l, a, p, q)];
+      }
+      const int es = sES[el2 * 6 + s];
+      const int mpq = orient_pq(es_orient(es), n - 1, p, q);
+      Gf[((size_t)(es_slave(es) * S + es_side(es)) * 15 + c) * n2 + mpq] = val;
+    }
+  } else {
     // one pass per line of direction l gives the values on both faces -l and +l;
     // the face node of the line has (p, q) = its free indices
     constexpr int P = C::P;
@@ -325,11 +407,16 @@ __global__ void __launch_bounds__(Cfg<n>::T) k_lift_vol(
       const int base = l == 0 ? P * line : (l == 1 ? p + P * n * q : p + P * q);
       const real* b = sbuf + (el2 * 15 + c) * n3p + base;
       real gm = real(0), gp = real(0);
+      if (LGL) {
+        gm = b[0];
+        gp = b[(n - 1) * stride];
+      } else {
 #pragma unroll
-      for (int a = 0; a < n; ++a) {
-        const real x = b[a * stride];
-        gm += ops.lm[a] * x;
-        gp += ops.lp[a] * x;
+        for (int a = 0; a < n; ++a) {
+          const real x = b[a * stride];
+          gm += ops.lm[a] * x;
+          gp += ops.lp[a] * x;
+        }
       }
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
@@ -377,7 +464,7 @@ __global__ void __launch_bounds__(Cfg<n>::T) k_lift_vol(
     node_sweep3<real, n>(sOp, myb, i, j, k, acc);
   } else {
     if constexpr (SW == 0)
-      line_sweep3<real, n>(sbuf, sOut, nullptr, 0, ops, tid);
+      line_sweep3<real, n, LGL>(sbuf, sOut, nullptr, 0, ops, tid);
     else
       tc_sweep3<n, NE, SW>(reinterpret_cast<const float*>(sbuf), reinterpret_cast<float*>(sOut), bfr, tid, T);
 #pragma unroll
@@ -435,7 +522,7 @@ __global__ void __launch_bounds__(128) k_face(const real* __restrict__ Wf, const
 // ---------------------------------------------------------------------------
 // a8-a10: surface integral, -1/J, RK stage update, face states of the new U
 // ---------------------------------------------------------------------------
-template <typename real, int n, int MODE>
+template <typename real, int n, int MODE, bool LGL>
 __global__ void __launch_bounds__(Cfg<n>::T) k_surf(
     const real* __restrict__ Ff, const int* __restrict__ elemSide, const real* __restrict__ sJ,
     const real* __restrict__ Utv, real* __restrict__ U, real* __restrict__ dU, real* __restrict__ Ut,
@@ -444,7 +531,7 @@ __global__ void __launch_bounds__(Cfg<n>::T) k_surf(
   using C = Cfg<n>;
   constexpr int n2 = C::n2, n3 = C::n3, NE = C::NE, T = C::T;
   __shared__ real sF[NE * 6 * NV * n2];
-  __shared__ real sU[(MODE == 1) ? NE * NV * n3 : 1];
+  __shared__ real sU[(MODE == 1) ? NE * NV * C::n3p : 1];
   __shared__ real sOp[n2 + 4 * n];
   __shared__ int sES[NE * 6];
   const int tid = threadIdx.x;
@@ -480,9 +567,18 @@ __global__ void __launch_bounds__(Cfg<n>::T) k_surf(
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       real s = Utv[((size_t)e * NV + v) * n3 + node];
-      s += c0 * Fe[(0 * NV + v) * n2 + pq0] + c1 * Fe[(1 * NV + v) * n2 + pq0];
-      s += c2 * Fe[(2 * NV + v) * n2 + pq1] + c3 * Fe[(3 * NV + v) * n2 + pq1];
-      s += c4 * Fe[(4 * NV + v) * n2 + pq2] + c5 * Fe[(5 * NV + v) * n2 + pq2];
+      if (LGL) {  // Gauss-Lobatto: only nodes on a face receive its flux
+        if (i == 0) s += c0 * Fe[(0 * NV + v) * n2 + pq0];
+        if (i == n - 1) s += c1 * Fe[(1 * NV + v) * n2 + pq0];
+        if (j == 0) s += c2 * Fe[(2 * NV + v) * n2 + pq1];
+        if (j == n - 1) s += c3 * Fe[(3 * NV + v) * n2 + pq1];
+        if (k == 0) s += c4 * Fe[(4 * NV + v) * n2 + pq2];
+        if (k == n - 1) s += c5 * Fe[(5 * NV + v) * n2 + pq2];
+      } else {
+        s += c0 * Fe[(0 * NV + v) * n2 + pq0] + c1 * Fe[(1 * NV + v) * n2 + pq0];
+        s += c2 * Fe[(2 * NV + v) * n2 + pq1] + c3 * Fe[(3 * NV + v) * n2 + pq1];
+        s += c4 * Fe[(4 * NV + v) * n2 + pq2] + c5 * Fe[(5 * NV + v) * n2 + pq2];
+      }
       ut[v] = -s * sj;
     }
     if (src.on) {
@@ -509,15 +605,15 @@ __global__ void __launch_bounds__(Cfg<n>::T) k_surf(
         const real un = U[g] + rk.B * du;
         dU[g] = du;
         U[g] = un;
-        sU[(el * NV + v) * n3 + node] = un;
+        sU[(el * NV + v) * C::n3p + pidx<n>(i, j, k)] = un;
       }
     } else {
 #pragma unroll
-      for (int v = 0; v < NV; ++v) sU[(el * NV + v) * n3 + node] = (v == 0 || v == 4) ? real(1) : real(0);
+      for (int v = 0; v < NV; ++v) sU[(el * NV + v) * C::n3p + pidx<n>(i, j, k)] = (v == 0 || v == 4) ? real(1) : real(0);
     }
     if (rk.prolong) {
       __syncthreads();
-      faces_from_volume<real, n>(sU, sOp, sES, e0, K, S, Wf, ph, status, tid);
+      faces_from_volume<real, n, LGL>(sU, ops, sES, e0, K, S, Wf, ph, status, tid);
     }
   }
 }
@@ -537,19 +633,22 @@ __global__ void __launch_bounds__(Cfg<n>::T) k_surf(
     default: return cudaErrorInvalidValue;         \
   }
 
-template <typename real, int n>
+template <typename real, int n, bool LGL = false>
 static cudaError_t prolong_n(const DevMesh& m, const real* U, const Ops<real>& ops, const Phys<real>& ph,
                              cudaStream_t st) {
   using C = Cfg<n>;
   const int grid = (m.K + C::NE - 1) / C::NE;
-  k_prolong<real, n><<<grid, C::T, 0, st>>>(U, m.elemSide, (real*)m.Wf, m.K, m.S, ops, ph, m.status);
+  k_prolong<real, n, LGL><<<grid, C::T, 0, st>>>(U, m.elemSide, (real*)m.Wf, m.K, m.S, ops, ph, m.status);
   return cudaGetLastError();
 }
 
 template <typename real>
 cudaError_t launch_prolong(const DevMesh& m, const real* U, const Ops<real>& ops, const Phys<real>& ph,
                            cudaStream_t st) {
-  FLEXI_DISPATCH_N(m.n, return prolong_n<real, NN>(m, U, ops, ph, st));
+  if (m.lgl) {
+    FLEXI_DISPATCH_N(m.n, return prolong_n<real, NN, true>(m, U, ops, ph, st));
+  }
+  FLEXI_DISPATCH_N(m.n, return prolong_n<real, NN, false>(m, U, ops, ph, st));
   return cudaSuccess;
 }
 
@@ -561,7 +660,7 @@ cudaError_t launch_bc(const DevMesh& m, double t, const Phys<real>& ph, cudaStre
   return cudaGetLastError();
 }
 
-template <typename real, int n, int SW>
+template <typename real, int n, int SW, bool LGL = false>
 static cudaError_t lift_vol_n(const DevMesh& m, const real* U, const Ops<real>& ops, const Phys<real>& ph,
                               int store_grad, cudaStream_t st) {
   using C = Cfg<n>;
@@ -569,14 +668,15 @@ static cudaError_t lift_vol_n(const DevMesh& m, const real* U, const Ops<real>& 
   static bool attr = false;
   if (!attr) {
     cudaError_t err =
-        cudaFuncSetAttribute(k_lift_vol<real, n, SW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_lift_vol<real, n, SW, LGL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     attr = true;
   }
   const int grid = (m.K + C::NE - 1) / C::NE;
-  k_lift_vol<real, n, SW><<<grid, C::T, smem, st>>>(U, (const real*)m.Ja, (const real*)m.sJ, (const real*)m.Wf,
-                                                    (const real*)m.fgeo, m.elemSide, (real*)m.Gf, (real*)m.Utv,
-                                                    store_grad ? (real*)m.Gvol : nullptr, m.K, m.S, ops, ph);
+  k_lift_vol<real, n, SW, LGL><<<grid, C::T, smem, st>>>(U, (const real*)m.Ja, (const real*)m.sJ,
+                                                         (const real*)m.Wf, (const real*)m.fgeo, m.elemSide,
+                                                         (real*)m.Gf, (real*)m.Utv,
+                                                         store_grad ? (real*)m.Gvol : nullptr, m.K, m.S, ops, ph);
   return cudaGetLastError();
 }
 
@@ -590,6 +690,9 @@ cudaError_t launch_lift_vol(const DevMesh& m, const real* U, const Ops<real>& op
       FLEXI_DISPATCH_N(m.n, return lift_vol_n<real, NN, 2>(m, U, ops, ph, store_grad, st));
     }
   }
+  if (m.lgl) {
+    FLEXI_DISPATCH_N(m.n, return lift_vol_n<real, NN, 0, true>(m, U, ops, ph, store_grad, st));
+  }
   FLEXI_DISPATCH_N(m.n, return lift_vol_n<real, NN, 0>(m, U, ops, ph, store_grad, st));
   return cudaSuccess;
 }
@@ -602,26 +705,29 @@ cudaError_t launch_face(const DevMesh& m, const Phys<real>& ph, cudaStream_t st)
   return cudaGetLastError();
 }
 
-template <typename real, int n>
+template <typename real, int n, bool LGL>
 static cudaError_t surf_n(const DevMesh& m, int mode, real* U, real* dU, real* Ut, const RkStage<real>& rk, double t,
                           const SourceParams& src, const Ops<real>& ops, const Phys<real>& ph, cudaStream_t st) {
   using C = Cfg<n>;
   const int grid = (m.K + C::NE - 1) / C::NE;
   if (mode == 0)
-    k_surf<real, n, 0><<<grid, C::T, 0, st>>>((const real*)m.Ff, m.elemSide, (const real*)m.sJ,
-                                              (const real*)m.Utv, U, dU, Ut, (real*)m.Wf, m.xsol, rk, t, src, m.K,
-                                              m.S, ops, ph, m.status);
+    k_surf<real, n, 0, LGL><<<grid, C::T, 0, st>>>((const real*)m.Ff, m.elemSide, (const real*)m.sJ,
+                                                   (const real*)m.Utv, U, dU, Ut, (real*)m.Wf, m.xsol, rk, t, src,
+                                                   m.K, m.S, ops, ph, m.status);
   else
-    k_surf<real, n, 1><<<grid, C::T, 0, st>>>((const real*)m.Ff, m.elemSide, (const real*)m.sJ,
-                                              (const real*)m.Utv, U, dU, Ut, (real*)m.Wf, m.xsol, rk, t, src, m.K,
-                                              m.S, ops, ph, m.status);
+    k_surf<real, n, 1, LGL><<<grid, C::T, 0, st>>>((const real*)m.Ff, m.elemSide, (const real*)m.sJ,
+                                                   (const real*)m.Utv, U, dU, Ut, (real*)m.Wf, m.xsol, rk, t, src,
+                                                   m.K, m.S, ops, ph, m.status);
   return cudaGetLastError();
 }
 
 template <typename real>
 cudaError_t launch_surf(const DevMesh& m, int mode, real* U, real* dU, real* Ut, const RkStage<real>& rk, double t,
                         const SourceParams& src, const Ops<real>& ops, const Phys<real>& ph, cudaStream_t st) {
-  FLEXI_DISPATCH_N(m.n, return surf_n<real, NN>(m, mode, U, dU, Ut, rk, t, src, ops, ph, st));
+  if (m.lgl) {
+    FLEXI_DISPATCH_N(m.n, return surf_n<real, NN, true>(m, mode, U, dU, Ut, rk, t, src, ops, ph, st));
+  }
+  FLEXI_DISPATCH_N(m.n, return surf_n<real, NN, false>(m, mode, U, dU, Ut, rk, t, src, ops, ph, st));
   return cudaSuccess;
 }
 

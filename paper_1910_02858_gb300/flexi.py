@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(HERE, "libflexi_gb300.so")
 
 FLEXI_OK, FLEXI_EINVAL, FLEXI_ENOMEM, FLEXI_ECUDA, FLEXI_EMESH, FLEXI_ENONPHYSICAL, FLEXI_EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
 NODES_GAUSS, NODES_LOBATTO = 0, 1
-RIEMANN_ROE, RIEMANN_HLLC, RIEMANN_ROE_SMOOTH = 0, 1, 2
+RIEMANN_ROE, RIEMANN_HLLC, RIEMANN_ROE_SMOOTH, RIEMANN_RUSANOV = 0, 1, 2, 3
 FP64, FP32, FP32_TF32, FP32_BF16 = 0, 1, 2, 3
 EXACT_TGV, EXACT_FREESTREAM, EXACT_MANUFACTURED = 0, 1, 2
 Q_K, Q_N, Q_NSIDES, Q_NBCSIDES, Q_DOF, Q_BYTES_PER_STAGE, Q_FLOPS_PER_STAGE, Q_STATUS, Q_DEVICE_BYTES, Q_PRECISION = range(10)

@@ -17,7 +17,7 @@ import torch
 
 import workloads as wl
 from oracle import equations as eq
-from oracle.dgsem import DGSEM, HLLC, ROE, Params
+from oracle.dgsem import DGSEM, HLLC, ROE, RUSANOV, Params
 
 pytestmark = pytest.mark.gpu
 
@@ -41,7 +41,7 @@ def _solver(cfg_kw, mesh):
 
 
 def _oracle(cfg_kw, mesh):
-    r = {0: ROE, 1: HLLC, 2: ROE}[cfg_kw.get("riemann", 0)]
+    r = {0: ROE, 1: HLLC, 2: ROE, 3: RUSANOV}[cfg_kw.get("riemann", 0)]
     bc = cfg_kw.get("bc_exact", 0)
     return DGSEM(Params(N=cfg_kw["N"], node_type=cfg_kw.get("node_type", 0), riemann=r,
                         smooth_roe=cfg_kw.get("riemann", 0) == 2, mu=cfg_kw.get("mu", 1 / 1600.0),
@@ -86,6 +86,8 @@ CASES = [
     ("pert_lg_N5_roesmooth", dict(nelem=(2, 2, 3), reorient_seed=5), dict(N=5, riemann=2, mu=1 / 400.0), "perturbed"),
     ("tgv_lg_N7_hllc", dict(nelem=(2, 2, 3), reorient_seed=6), dict(N=7, riemann=1), "tgv"),
     ("pert_lgl_N6_hllc", dict(nelem=(2, 2, 2), reorient_seed=7), dict(N=6, node_type=1, riemann=1), "perturbed"),
+    ("pert_lg_N5_rusanov", dict(nelem=(3, 2, 2), reorient_seed=9), dict(N=5, riemann=3), "perturbed"),
+    ("tgv_lgl_N4_rusanov", dict(nelem=(2, 3, 2), reorient_seed=10), dict(N=4, node_type=1, riemann=3), "tgv"),
     ("curved_fs_lg_N4", dict(nelem=(3, 2, 2), lo=(-1,) * 3, hi=(1,) * 3, Ngeo=4, mapping="sine",
                              periodic=(False,) * 3, reorient_seed=8),
      dict(N=4, Ngeo=4, riemann=1, bc_exact=1), "perturbed_small"),

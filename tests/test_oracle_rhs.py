@@ -11,7 +11,7 @@ import torch
 
 import workloads as wl
 from oracle import equations as eq
-from oracle.dgsem import DGSEM, HLLC, ROE, Params
+from oracle.dgsem import DGSEM, HLLC, ROE, RUSANOV, Params
 
 GAS = eq.Gas(1.4, 0.72, 1.0 / 1600.0)
 
@@ -73,11 +73,12 @@ def _rand_normals(n, seed):
     return T(v / np.linalg.norm(v, axis=1, keepdims=True))
 
 
-@pytest.mark.parametrize("kind", ["roe", "roe_smooth", "hllc"])
+@pytest.mark.parametrize("kind", ["roe", "roe_smooth", "hllc", "rusanov"])
 def test_riemann_consistency_and_symmetry(kind):
     f = {"roe": lambda a, b, n: eq.riemann_roe(a, b, n, GAS),
          "roe_smooth": lambda a, b, n: eq.riemann_roe(a, b, n, GAS, smooth=True),
-         "hllc": lambda a, b, n: eq.riemann_hllc(a, b, n, GAS)}[kind]
+         "hllc": lambda a, b, n: eq.riemann_hllc(a, b, n, GAS),
+         "rusanov": lambda a, b, n: eq.riemann_rusanov(a, b, n, GAS)}[kind]
     UL, UR, n = _rand_states(50, 1), _rand_states(50, 2), _rand_normals(50, 3)
     F = eq.normal_flux(eq.flux_conv(UL, eq.prim(UL, GAS)), n)
     assert torch.allclose(f(UL, UL, n), F, rtol=1e-13, atol=1e-13)
@@ -102,6 +103,17 @@ def test_riemann_supersonic_upwinding(kind):
     assert torch.allclose(f(UL2, UR2, n), FR2, rtol=1e-13, atol=1e-13)
 
 
+def test_rusanov_closed_form():
+    """Scalar-dissipation flux: the jump is damped by the largest local wave speed."""
+    n = T([[1.0, 0.0, 0.0]])
+    WL, WR = T([[1.0, 0.5, 0.0, 0.0, 1.0]]), T([[1.0, 0.5, 0.0, 0.0, 2.0]])
+    UL, UR = eq.cons(WL, GAS), eq.cons(WR, GAS)
+    lam = max(0.5 + math.sqrt(1.4 * 1.0), 0.5 + math.sqrt(1.4 * 2.0))
+    FL = eq.normal_flux(eq.flux_conv(UL, WL), n)
+    FR = eq.normal_flux(eq.flux_conv(UR, WR), n)
+    assert torch.allclose(eq.riemann_rusanov(UL, UR, n, GAS), 0.5 * (FL + FR) - 0.5 * lam * (UR - UL), rtol=1e-15)
+
+
 def test_hllc_resolves_stationary_contact():
     n = T([[1.0, 0.0, 0.0]])
     WL, WR = T([[1.0, 0.0, 0.3, 0.0, 1.0]]), T([[0.2, 0.0, -0.5, 0.1, 1.0]])
@@ -118,7 +130,7 @@ def _dg(nelem, N, nt, riemann=ROE, mapping="cartesian", periodic=True, reo=None,
 
 
 @pytest.mark.parametrize("nt", [0, 1])
-@pytest.mark.parametrize("riemann", [ROE, HLLC])
+@pytest.mark.parametrize("riemann", [ROE, HLLC, RUSANOV])
 def test_freestream_curved(nt, riemann):
     """Free-stream preservation on a curved mesh (Sec. 3.1, curl metrics)."""
     N = 4
@@ -130,7 +142,7 @@ def test_freestream_curved(nt, riemann):
 
 
 @pytest.mark.parametrize("nt", [0, 1])
-@pytest.mark.parametrize("riemann", [ROE, HLLC])
+@pytest.mark.parametrize("riemann", [ROE, HLLC, RUSANOV])
 @pytest.mark.parametrize("state", ["tgv", "perturbed"])
 def test_conservation_periodic(nt, riemann, state):
     """sum_nodes w J U_t = 0 for all five conserved variables (the side flux is
