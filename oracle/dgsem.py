@@ -72,6 +72,7 @@ class Params:
     Ma: float = 0.1  # for the TGV exact state used as boundary data
     bc_exact: object = eq.EXACT_TGV  # exact function id (or callable (x, t) -> U) on Dirichlet sides
     source: bool = False  # manufactured-solution source term
+    split: str = ""  # "" standard weak form; "pirozzoli" / "central": split form (LGL only)
 
 
 class DGSEM:
@@ -149,18 +150,21 @@ class DGSEM:
         # a6, a7: volume integral
         Uv, Wv = U.movedim(1, -1), W.movedim(1, -1)
         Gv = G.permute(0, 3, 4, 5, 1, 2)  # [K,n,n,n,3,5]
-        F = eq.flux_conv(Uv, Wv) - eq.flux_visc(Wv, Gv, gas)  # [K,n,n,n,3,5]
-        vol = torch.zeros_like(U)
-        for l in range(3):
-            Fl = sum(Ja[:, l, d].unsqueeze(-1) * F[..., d, :] for d in range(3))  # [K,n,n,n,5]
-            vol = vol + apply_dir(b.Dhat, Fl.movedim(-1, 1), l)
+        Ff = geo.to_elements(fstar, -fstar)  # [K,6,5,q,p] outward f* s of every element face
+        if self.p.split:
+            vol, surf = self._split_form(U, Uv, Wv, Gv, Ff)
+        else:
+            F = eq.flux_conv(Uv, Wv) - eq.flux_visc(Wv, Gv, gas)  # [K,n,n,n,3,5]
+            vol = torch.zeros_like(U)
+            for l in range(3):
+                Fl = sum(Ja[:, l, d].unsqueeze(-1) * F[..., d, :] for d in range(3))  # [K,n,n,n,5]
+                vol = vol + apply_dir(b.Dhat, Fl.movedim(-1, 1), l)
 
-        # a8: surface integral
-        Ff = geo.to_elements(fstar, -fstar)  # [K,6,5,q,p]
-        surf = torch.zeros_like(U)
-        for s in range(6):
-            l, sgn = s // 2, (-1 if s % 2 == 0 else 1)
-            surf = surf + spread(Ff[:, s], b.lhat_side(sgn), l)
+            # a8: surface integral
+            surf = torch.zeros_like(U)
+            for s in range(6):
+                l, sgn = s // 2, (-1 if s % 2 == 0 else 1)
+                surf = surf + spread(Ff[:, s], b.lhat_side(sgn), l)
 
         # a9
         Ut = -(vol + surf) / J
@@ -169,6 +173,39 @@ class DGSEM:
         if parts:
             return Ut, dict(W=W, G=G, fstar=fstar, vol=vol, surf=surf, Wstar=Wstar, UL=UL, UR=UR, GL=GL, GR=GR)
         return Ut
+
+    def _split_form(self, U, Uv, Wv, Gv, Ff):
+        """Split-form volume and surface terms (Sec. 3.3, Eq. semiDiscreteSplit) on
+        Gauss-Lobatto nodes: advective volume term 2 sum_a D_ia Fcal#^l(U_i, U_a)
+        with metric-averaged two-point fluxes, viscous volume term in strong form
+        -sum_l D^(l) Fcal^{v,l}, and the strong-form surface penalty
+        l_hat(+-1) [f* s - Fcal.N] with the outward reference normal N = +-1 and
+        Fcal the element's own total contravariant flux on the face."""
+        if self.p.node_type != 1:
+            raise ValueError("the split form needs Gauss-Lobatto nodes (summation by parts)")
+        geo, b, gas = self.geo, self.b, self.gas
+        Ja = geo.Ja
+        Fc = eq.flux_conv(Uv, Wv)
+        Fv = eq.flux_visc(Wv, Gv, gas)
+        vol = torch.zeros_like(U)
+        surf = torch.zeros_like(U)
+        for l in range(3):
+            Jl = Ja[:, l].movedim(1, -1)  # [K,n,n,n,3] row Ja^l_.
+            # two-point fluxes along lines of direction l: axis 3 - l of [K,k,j,i]
+            ax = 3 - l
+            ul, wl, jl = Uv.movedim(ax, -2), Wv.movedim(ax, -2), Jl.movedim(ax, -2)  # [..., n(line), 5]
+            Fs = eq.two_point_contravariant(ul.unsqueeze(-2), wl.unsqueeze(-2), ul.unsqueeze(-3), wl.unsqueeze(-3),
+                                            jl.unsqueeze(-2), jl.unsqueeze(-3), self.p.split)  # [..., i, a, 5]
+            adv = 2.0 * torch.einsum("ia,...iav->...iv", b.D, Fs)
+            vol = vol + adv.movedim(-2, ax).movedim(-1, 1)
+            Fvl = sum(Ja[:, l, d].unsqueeze(-1) * Fv[..., d, :] for d in range(3)).movedim(-1, 1)
+            Fcl = sum(Ja[:, l, d].unsqueeze(-1) * Fc[..., d, :] for d in range(3)).movedim(-1, 1)
+            vol = vol - apply_dir(b.D, Fvl, l)
+            for sgn in (-1, 1):
+                s = 2 * l + (0 if sgn < 0 else 1)
+                interior = prolong(Fcl - Fvl, b.l_side(sgn), l)  # [K,5,q,p]
+                surf = surf + spread(Ff[:, s] - sgn * interior, b.lhat_side(sgn), l)
+        return vol, surf
 
     def source(self, t: float) -> torch.Tensor:
         x = self.geo.x.movedim(1, -1)  # [K,n,n,n,3]

@@ -184,6 +184,36 @@ def riemann_hllc(UL, UR, n, gas):
 
 
 # ---------------------------------------------------------------------------
+# two-point volume fluxes of the split form (Sec. 3.3, Eq. semiDiscreteSplit)
+# ---------------------------------------------------------------------------
+
+
+def two_point_contravariant(Ua, Wa, Ub, Wb, Ja_a, Ja_b, kind: str):
+    """Contravariant two-point flux sum_d F#_d(U_a, U_b) * (Ja_d(a) + Ja_d(b)) / 2.
+
+    kind "pirozzoli": kinetic-energy-preserving flux of Pirozzoli (2011), the one
+    of the paper's NACA 64418 computation (Sec. 7.1): with arithmetic means {.},
+    F#_rho = {rho}{u_d}, F#_m = {rho}{u_d}{u} + {p} e_d, F#_E = {rho}{u_d}{H},
+    H = (rho E + p) / rho.  kind "central": (F(U_a) + F(U_b)) / 2 (standard DG).
+    Variables last; Ja_* are [..., 3] (the row Ja^l_. of the sweep direction l).
+    """
+    Jm = 0.5 * (Ja_a + Ja_b)
+    if kind == "central":
+        Fa = flux_conv(Ua, Wa)  # [..., 3, 5]
+        Fb = flux_conv(Ub, Wb)
+        return 0.5 * ((Fa + Fb) * Jm.unsqueeze(-1)).sum(-2)
+    rho = 0.5 * (Wa[..., 0] + Wb[..., 0])
+    vel = 0.5 * (Wa[..., 1:4] + Wb[..., 1:4])
+    p = 0.5 * (Wa[..., 4] + Wb[..., 4])
+    Ha = (Ua[..., 4] + Wa[..., 4]) / Wa[..., 0]
+    Hb = (Ub[..., 4] + Wb[..., 4]) / Wb[..., 0]
+    H = 0.5 * (Ha + Hb)
+    uc = (vel * Jm).sum(-1)  # contravariant mean velocity
+    m = rho * uc
+    return torch.cat([m.unsqueeze(-1), m.unsqueeze(-1) * vel + p.unsqueeze(-1) * Jm, (m * H).unsqueeze(-1)], dim=-1)
+
+
+# ---------------------------------------------------------------------------
 # exact solutions used as Dirichlet data and source terms (Sec. 2.2 names
 # Dirichlet boundaries; the fields themselves are the test cases' definitions)
 # ---------------------------------------------------------------------------
