@@ -443,25 +443,37 @@ def extras(args, s64, U0, mesh, dt, dev, F, wl, Solver, SolverConfig, torch, np)
 
 def lobatto_pid(mesh, dt, dev, F, wl, Solver, SolverConfig, torch):
     """The same 16^3, N = 7 Taylor-Green step on Gauss-Lobatto nodes (prolongation
-    is a copy, face terms touch only face nodes), FP64 and FP32."""
+    is a copy, face terms touch only face nodes), FP64 and FP32, with the standard
+    and with the split-form (kinetic-energy-preserving) volume integral."""
     res = {}
     x = mesh.node_coords(7, 1)
-    for name, prec in (("fp64", F.FP64), ("fp32", F.FP32)):
-        s = Solver(SolverConfig(N=7, node_type=F.NODES_LOBATTO, riemann=F.RIEMANN_HLLC, precision=prec),
-                   mesh.coords, mesh.conn, device=dev)
-        U = torch.tensor(wl.taylor_green(x), device=dev, dtype=s.dtype)
-        dU = torch.zeros_like(U)
-        for _ in range(3):
-            s.step(U, dU, 0.0, dt)
-        torch.cuda.synchronize(dev)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for k in range(10):
-            s.step(U, dU, k * dt, dt)
-        e1.record()
-        torch.cuda.synchronize(dev)
-        res[name] = {"pid": e0.elapsed_time(e1) * 1e6 / (10 * NSTAGES * s.query(F.Q_DOF)), "steps": 10}
-        s.close()
+    for name, prec, split in (("fp64", F.FP64, F.SPLIT_STANDARD), ("fp32", F.FP32, F.SPLIT_STANDARD),
+                              ("fp64_split_kep", F.FP64, F.SPLIT_KEP), ("fp32_split_kep", F.FP32, F.SPLIT_KEP)):
+        s = Solver(SolverConfig(N=7, node_type=F.NODES_LOBATTO, riemann=F.RIEMANN_HLLC, precision=prec,
+                                split_form=split), mesh.coords, mesh.conn, device=dev)
+        try:
+            U = torch.tensor(wl.taylor_green(x), device=dev, dtype=s.dtype)
+            dU = torch.zeros_like(U)
+            for _ in range(3):
+                s.step(U, dU, 0.0, dt)
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for k in range(10):
+                s.step(U, dU, k * dt, dt)
+            e1.record()
+            torch.cuda.synchronize(dev)
+            ms = e0.elapsed_time(e1)
+            F.flexi_profile(s.ctx, True)
+            for k in range(2):
+                s.step(U, dU, k * dt, dt)
+            torch.cuda.synchronize(dev)
+            kt = F.flexi_kernel_times(s.ctx, reset=True)
+            F.flexi_profile(s.ctx, False)
+            res[name] = {"pid": ms * 1e6 / (10 * NSTAGES * s.query(F.Q_DOF)), "steps": 10,
+                         "lift_vol_ms_per_launch": kt["lift_vol"][0] / max(kt["lift_vol"][1], 1)}
+        finally:
+            s.close()
     return res
 
 

@@ -62,6 +62,12 @@ enum { FLEXI_RIEMANN_ROE = 0, FLEXI_RIEMANN_HLLC = 1, FLEXI_RIEMANN_ROE_SMOOTH =
  * with the D-matrix line sweeps on tensor cores in TF32 or BF16, each operand
  * split into three terms of the narrow type (six products, FP32 accumulation). */
 enum { FLEXI_FP64 = 0, FLEXI_FP32 = 1, FLEXI_FP32_TF32 = 2, FLEXI_FP32_BF16 = 3 };
+/* Volume integral (Sec. 3.3): STANDARD is the weak form of Eq. semiDiscrete; KEP is
+ * the split form of Eq. semiDiscreteSplit on Gauss-Lobatto nodes, 2 sum_a D_ia
+ * F#(U_i, U_a) with Pirozzoli's kinetic-energy-preserving two-point flux (the
+ * flux of the paper's NACA 64418 computation, Sec. 7.1) and metric terms averaged
+ * over each pair; viscous fluxes stay in the standard form. */
+enum { FLEXI_SPLIT_STANDARD = 0, FLEXI_SPLIT_KEP = 1 };
 /* Exact states for Dirichlet sides (and the manufactured source term). */
 enum { FLEXI_EXACT_TGV = 0, FLEXI_EXACT_FREESTREAM = 1, FLEXI_EXACT_MANUFACTURED = 2 };
 
@@ -73,7 +79,7 @@ typedef struct {
   int precision;  /* FLEXI_FP64 / FLEXI_FP32 / FLEXI_FP32_TF32 / FLEXI_FP32_BF16 */
   int bc_exact;   /* FLEXI_EXACT_* used on every Dirichlet side */
   int source;     /* 1: add the manufactured-solution source term */
-  int reserved;
+  int split_form; /* FLEXI_SPLIT_*; FLEXI_SPLIT_KEP needs FLEXI_NODES_LOBATTO and FP64 or FP32 */
   double gamma, Pr, mu; /* ideal gas, constant viscosity (Stokes' hypothesis) */
   double Ma;            /* Mach number of the Taylor-Green exact state */
 } flexi_params;
@@ -89,7 +95,8 @@ typedef struct {
  * Computes on the device: x at the solution nodes, curl-form metrics Ja, 1/J,
  * face normals and surface elements; allocates every buffer later calls use.
  * Returns FLEXI_EMESH for asymmetric connectivity or J <= 0, FLEXI_EINVAL for
- * bad sizes or parameters.  On success *out owns everything; free it with
+ * bad sizes or parameters, FLEXI_EUNSUPPORTED for the split form with Gauss
+ * nodes or a tensor-core form.  On success *out owns everything; free it with
  * flexi_destroy.  The call synchronises `stream`. */
 flexi_status flexi_mesh_init(flexi_ctx **out, const flexi_params *p, int K, const double *coords,
                              const int32_t *conn, void *stream);
@@ -115,7 +122,7 @@ flexi_status flexi_rk_step_stages(flexi_ctx *ctx, void *U, void *dU, double t, d
  * U_stages: device [5][K][5][n^3] as written by flexi_rk_step_stages;
  * lamU, lam_dU: device, updated in place.  Requires FLEXI_FP64 or FLEXI_FP32
  * and a Roe-type flux (ROE or ROE_SMOOTH); periodic meshes without source term
- * only (FLEXI_EUNSUPPORTED otherwise). */
+ * and with the standard volume integral only (FLEXI_EUNSUPPORTED otherwise). */
 flexi_status flexi_adjoint_step(flexi_ctx *ctx, const void *U_stages, void *lamU, void *lam_dU, double t,
                                 double dt, void *stream);
 

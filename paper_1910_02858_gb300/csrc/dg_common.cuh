@@ -20,6 +20,7 @@ struct Ops {
   real lm[MAXN], lp[MAXN];  // l_j(-1), l_j(+1)
   real lhm[MAXN], lhp[MAXN];  // l_j(-1)/w_j, l_j(+1)/w_j
   real w[MAXN];
+  real DT[MAXN * MAXN];  // DT[a * n + i] = D[i][a]  (strong-form derivative, split form only)
 };
 
 template <typename real>

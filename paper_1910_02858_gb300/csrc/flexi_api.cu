@@ -187,6 +187,7 @@ void fill_ops(Ops<real>& o, const std::vector<double>& D, const std::vector<doub
     for (int a = 0; a < n; ++a) {
       const double dhat = -(w[a] / w[i]) * D[a * n + i];  // Dhat[i][a] = -(w_a/w_i) D_ai
       o.DhatT[a * n + i] = (real)dhat;
+      o.DT[a * n + i] = (real)D[i * n + a];
     }
   for (int i = 0; i < n; ++i) {
     o.lm[i] = (real)lm[i];
@@ -412,6 +413,7 @@ flexi_status mesh_init_impl(flexi_ctx* c, const flexi_params* p, int K, const do
   c->m.status = c->status;
   c->m.sweep_mode = p->precision == FLEXI_FP32_TF32 ? 1 : (p->precision == FLEXI_FP32_BF16 ? 2 : 0);
   c->m.lgl = p->node_type == FLEXI_NODES_LOBATTO ? 1 : 0;
+  c->m.split = p->split_form == FLEXI_SPLIT_KEP ? 1 : 0;
   const size_t rs = c->rs;
   if (c->fp64) {
     c->m.Ja = c->Ja64; c->m.sJ = c->sJ64; c->m.fgeo = c->fgeo64;
@@ -564,6 +566,10 @@ flexi_status flexi_mesh_init(flexi_ctx** out, const flexi_params* p, int K, cons
   if (p->node_type != FLEXI_NODES_GAUSS && p->node_type != FLEXI_NODES_LOBATTO) return FLEXI_EINVAL;
   if (p->riemann < 0 || p->riemann > 3 || p->bc_exact < 0 || p->bc_exact > 2) return FLEXI_EINVAL;
   if (p->precision < FLEXI_FP64 || p->precision > FLEXI_FP32_BF16) return FLEXI_EINVAL;
+  if (p->split_form != FLEXI_SPLIT_STANDARD && p->split_form != FLEXI_SPLIT_KEP) return FLEXI_EINVAL;
+  if (p->split_form == FLEXI_SPLIT_KEP &&
+      (p->node_type != FLEXI_NODES_LOBATTO || (p->precision != FLEXI_FP64 && p->precision != FLEXI_FP32)))
+    return FLEXI_EUNSUPPORTED;
   if (!(p->gamma > 1.0) || !(p->Pr > 0.0) || !(p->mu >= 0.0)) return FLEXI_EINVAL;
   if ((long long)K * 6 >= (1LL << 27)) return FLEXI_EUNSUPPORTED;
   flexi_ctx* c = new (std::nothrow) flexi_ctx();
@@ -601,7 +607,7 @@ flexi_status flexi_rk_step_stages(flexi_ctx* c, void* U, void* dU, double t, dou
 
 static bool adjoint_supported(const flexi_ctx* c) {
   return c->nBC == 0 && (c->p.riemann == FLEXI_RIEMANN_ROE || c->p.riemann == FLEXI_RIEMANN_ROE_SMOOTH) &&
-         !c->p.source;
+         !c->p.source && c->p.split_form == FLEXI_SPLIT_STANDARD;
 }
 
 flexi_status flexi_adjoint_step(flexi_ctx* c, const void* U_stages, void* lamU, void* lam_dU, double t, double dt,

@@ -236,8 +236,10 @@ __global__ void k_bc(const double* __restrict__ xbc, real* __restrict__ Wf, int 
 // ---------------------------------------------------------------------------
 // a2-a4, a6, a7: lifting, gradient prolongation, volume integral
 // ---------------------------------------------------------------------------
-// SW: 0 line sweeps on the FP32/FP64 pipes; 1 TF32 and 2 BF16 3-term split mma (float only)
-template <typename real, int n, int SW, bool LGL>
+// SW: 0 line sweeps on the FP32/FP64 pipes; 1 TF32 and 2 BF16 3-term split mma (float only).
+// SPLIT (Gauss-Lobatto, SW = 0 only): the split-form volume integral of Sec. 3.3
+// (Eq. semiDiscreteSplit) with the kinetic-energy-preserving two-point flux.
+template <typename real, int n, int SW, bool LGL, bool SPLIT = false>
 __global__ void __launch_bounds__(Cfg<n>::T) k_lift_vol(
     const real* __restrict__ U, const real* __restrict__ Ja, const real* __restrict__ sJ,
     const real* __restrict__ Wf, const real* __restrict__ fgeo, const int* __restrict__ elemSide,
@@ -250,8 +252,9 @@ __global__ void __launch_bounds__(Cfg<n>::T) k_lift_vol(
   constexpr int nout = (sizeof(real) == 8 && SW == 0) ? 0 : NE * NV * n3p;
   real* sOut = sbuf + NE * 15 * n3p;               // [NE][5][n3p]  sweep results (not for FP64)
   real* sQ = sOut + nout;                          // [NE][6][15][n2]  (v*3+d)
-  real* sOp = sQ + NE * 6 * 15 * n2;               // DhatT, lm, lp, lhm, lhp
-  int* sES = reinterpret_cast<int*>(sOp + n2 + 4 * n);
+  real* sOp = sQ + NE * 6 * 15 * n2;               // DhatT, lm, lp, lhm, lhp (+ DT with SPLIT)
+  int* sES = reinterpret_cast<int*>(sOp + n2 + 4 * n + (SPLIT ? n2 : 0));
+  static_assert(!SPLIT || (LGL && SW == 0), "the split form is built on Gauss-Lobatto nodes with CUDA-core sweeps");
 
   const int tid = threadIdx.x;
   const int el = tid / n3, node = tid - el * n3;
@@ -262,6 +265,8 @@ __global__ void __launch_bounds__(Cfg<n>::T) k_lift_vol(
   const int pn = pidx<n>(i, j, k);
 
   load_ops<real, n>(sOp, ops, tid, T);
+  if constexpr (SPLIT)
+    for (int t = tid; t < n2; t += T) sOp[n2 + 4 * n + t] = ops.DT[t];
   for (int t = tid; t < NE * 6; t += T) sES[t] = (e0 + t / 6 < K) ? elemSide[(size_t)e0 * 6 + t] : 0;
 
   real Uo[NV], W[NV], jac[9], sj;
@@ -428,6 +433,88 @@ __global__ void __launch_bounds__(Cfg<n>::T) k_lift_vol(
   }
   __syncthreads();
 
+  if constexpr (SPLIT) {
+    // Split form (Eq. semiDiscreteSplit).  Viscous part in weak form: D_hat sweeps of
+    // -Fcal^{v,l} = -sum_d Ja^l_d F^v_d; on Gauss-Lobatto nodes D_hat = D - M^{-1} B
+    // (summation by parts), so this is the strong form -D Fcal^{v,l} plus its face terms.
+    real acc[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[v] = real(0);
+    __syncthreads();
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+      const real nl[3] = {jac[l * 3], jac[l * 3 + 1], jac[l * 3 + 2]};
+      real fv[NV];
+      visc_normal(W, G, nl, ph, fv);  // linear in its direction argument
+#pragma unroll
+      for (int v = 0; v < NV; ++v) myb[(l * NV + v) * n3p + pn] = -fv[v];
+    }
+    __syncthreads();
+    if constexpr (sizeof(real) == 8) {
+      node_sweep3<real, n>(sOp, myb, i, j, k, acc);
+    } else {
+      line_sweep3<real, n, true>(sbuf, sOut, nullptr, 0, ops, tid);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) acc[v] = sOut[(el * NV + v) * n3p + pn];
+    }
+    __syncthreads();
+    // Advective part: 2 sum_a D_{i_l a} Fcal#^l(node, node with index_l = a) with the
+    // kinetic-energy-preserving flux of Pirozzoli and metric terms averaged over the
+    // pair.  Staged per node: rho, u, v, w, p, H = (rho E + p)/rho, Ja (9).
+#pragma unroll
+    for (int c = 0; c < NV; ++c) myb[c * n3p + pn] = W[c];
+    const real H = (Uo[4] + W[4]) / W[0];
+    myb[5 * n3p + pn] = H;
+#pragma unroll
+    for (int c = 0; c < 9; ++c) myb[(6 + c) * n3p + pn] = jac[c];
+    __syncthreads();
+    const real* sD = sOp + n2 + 4 * n;  // DT[a * n + i] = D[i][a]
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+      const int il = l == 0 ? i : (l == 1 ? j : k);
+      const real J0 = jac[l * 3], J1 = jac[l * 3 + 1], J2 = jac[l * 3 + 2];
+      real sm[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) sm[v] = real(0);
+#pragma unroll
+      for (int a = 0; a < n; ++a) {
+        const int pa = l == 0 ? pidx<n>(a, j, k) : (l == 1 ? pidx<n>(i, a, k) : pidx<n>(i, j, a));
+        const real* f = myb + pa;
+        // pair sums (twice the arithmetic means)
+        const real rs = W[0] + f[0], us = W[1] + f[n3p], vs = W[2] + f[2 * n3p], ws = W[3] + f[3 * n3p];
+        const real ps = W[4] + f[4 * n3p], Hs = H + f[5 * n3p];
+        const real j0 = J0 + f[(6 + 3 * l) * n3p], j1 = J1 + f[(7 + 3 * l) * n3p], j2 = J2 + f[(8 + 3 * l) * n3p];
+        const real m = real(0.125) * rs * (us * j0 + vs * j1 + ws * j2);  // {rho} {u . Ja^l}
+        const real d = sD[a * n + il];
+        const real dm = d * m, dp = real(0.5) * d * ps;
+        // 2 D F#: mass 2 dm; momentum dm u_s + (d p_s / 2) Ja_s; energy dm H_s
+        sm[0] += dm;
+        sm[1] += dm * us + dp * j0;
+        sm[2] += dm * vs + dp * j1;
+        sm[3] += dm * ws + dp * j2;
+        sm[4] += dm * Hs;
+      }
+      acc[0] += real(2) * sm[0];
+#pragma unroll
+      for (int v = 1; v < NV; ++v) acc[v] += sm[v];
+      // face terms of the strong form: -(+-1) l_hat(+-1) Fcal^{c,l} at the line's end nodes
+      if (il == 0 || il == n - 1) {
+        const real c = il == 0 ? sOp[n2 + 2 * n] : -sOp[n2 + 3 * n + n - 1];
+        const real uc = W[1] * J0 + W[2] * J1 + W[3] * J2;
+        const real mf = Uo[1] * J0 + Uo[2] * J1 + Uo[3] * J2;
+        acc[0] += c * mf;
+        acc[1] += c * (Uo[1] * uc + W[4] * J0);
+        acc[2] += c * (Uo[2] * uc + W[4] * J1);
+        acc[3] += c * (Uo[3] * uc + W[4] * J2);
+        acc[4] += c * (uc * (Uo[4] + W[4]));
+      }
+    }
+    if (valid) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) Utv[((size_t)e * NV + v) * n3 + node] = acc[v];
+    }
+    return;
+  }
   // a6: contravariant fluxes Fcal^l = sum_d Ja^l_d (F^c_d - F^v_d): in registers for
   // FP32, accumulated in shared memory for FP64 (register budget)
   if constexpr (sizeof(real) == 4) {
@@ -476,12 +563,12 @@ __global__ void __launch_bounds__(Cfg<n>::T) k_lift_vol(
   }
 }
 
-template <typename real, int n, int SW>
+template <typename real, int n, int SW, bool SPLIT = false>
 constexpr size_t lift_vol_smem() {
   using C = Cfg<n>;
   // the FP64 form sweeps per node and needs no result buffer
   constexpr int out = (sizeof(real) == 8 && SW == 0) ? 0 : C::NE * NV * C::n3p;
-  return sizeof(real) * (C::NE * 15 * C::n3p + out + C::NE * 6 * 15 * C::n2 + C::n2 + 4 * n) +
+  return sizeof(real) * (C::NE * 15 * C::n3p + out + C::NE * 6 * 15 * C::n2 + C::n2 + 4 * n + (SPLIT ? C::n2 : 0)) +
          sizeof(int) * C::NE * 6;
 }
 
@@ -660,20 +747,20 @@ cudaError_t launch_bc(const DevMesh& m, double t, const Phys<real>& ph, cudaStre
   return cudaGetLastError();
 }
 
-template <typename real, int n, int SW, bool LGL = false>
+template <typename real, int n, int SW, bool LGL = false, bool SPLIT = false>
 static cudaError_t lift_vol_n(const DevMesh& m, const real* U, const Ops<real>& ops, const Phys<real>& ph,
                               int store_grad, cudaStream_t st) {
   using C = Cfg<n>;
-  constexpr size_t smem = lift_vol_smem<real, n, SW>();
+  constexpr size_t smem = lift_vol_smem<real, n, SW, SPLIT>();
   static bool attr = false;
   if (!attr) {
-    cudaError_t err =
-        cudaFuncSetAttribute(k_lift_vol<real, n, SW, LGL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t err = cudaFuncSetAttribute(k_lift_vol<real, n, SW, LGL, SPLIT>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     attr = true;
   }
   const int grid = (m.K + C::NE - 1) / C::NE;
-  k_lift_vol<real, n, SW, LGL><<<grid, C::T, smem, st>>>(U, (const real*)m.Ja, (const real*)m.sJ,
+  k_lift_vol<real, n, SW, LGL, SPLIT><<<grid, C::T, smem, st>>>(U, (const real*)m.Ja, (const real*)m.sJ,
                                                          (const real*)m.Wf, (const real*)m.fgeo, m.elemSide,
                                                          (real*)m.Gf, (real*)m.Utv,
                                                          store_grad ? (real*)m.Gvol : nullptr, m.K, m.S, ops, ph);
@@ -689,6 +776,9 @@ cudaError_t launch_lift_vol(const DevMesh& m, const real* U, const Ops<real>& op
     } else if (m.sweep_mode == 2) {
       FLEXI_DISPATCH_N(m.n, return lift_vol_n<real, NN, 2>(m, U, ops, ph, store_grad, st));
     }
+  }
+  if (m.lgl && m.split) {
+    FLEXI_DISPATCH_N(m.n, return lift_vol_n<real, NN, 0, true, true>(m, U, ops, ph, store_grad, st));
   }
   if (m.lgl) {
     FLEXI_DISPATCH_N(m.n, return lift_vol_n<real, NN, 0, true>(m, U, ops, ph, store_grad, st));

@@ -19,6 +19,7 @@ NODES_GAUSS, NODES_LOBATTO = 0, 1
 RIEMANN_ROE, RIEMANN_HLLC, RIEMANN_ROE_SMOOTH, RIEMANN_RUSANOV = 0, 1, 2, 3
 FP64, FP32, FP32_TF32, FP32_BF16 = 0, 1, 2, 3
 EXACT_TGV, EXACT_FREESTREAM, EXACT_MANUFACTURED = 0, 1, 2
+SPLIT_STANDARD, SPLIT_KEP = 0, 1
 Q_K, Q_N, Q_NSIDES, Q_NBCSIDES, Q_DOF, Q_BYTES_PER_STAGE, Q_FLOPS_PER_STAGE, Q_STATUS, Q_DEVICE_BYTES, Q_PRECISION = range(10)
 KERNEL_CLASSES = ["lift_vol", "face", "surf_rk", "prolong", "bc", "adjoint", "reduce", "other"]
 
@@ -32,7 +33,7 @@ NOALLOC_MAX_ELEMENTS = 65536
 class flexi_params(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int), ("Ngeo", ctypes.c_int), ("node_type", ctypes.c_int), ("riemann", ctypes.c_int),
                 ("precision", ctypes.c_int), ("bc_exact", ctypes.c_int), ("source", ctypes.c_int),
-                ("reserved", ctypes.c_int), ("gamma", ctypes.c_double), ("Pr", ctypes.c_double),
+                ("split_form", ctypes.c_int), ("gamma", ctypes.c_double), ("Pr", ctypes.c_double),
                 ("mu", ctypes.c_double), ("Ma", ctypes.c_double)]
 
 

@@ -21,6 +21,7 @@ class SolverConfig:
     precision: int = F.FP64
     bc_exact: int = F.EXACT_TGV
     source: bool = False
+    split_form: int = F.SPLIT_STANDARD
     gamma: float = 1.4
     Pr: float = 0.72
     mu: float = 1.0 / 1600.0
@@ -29,7 +30,7 @@ class SolverConfig:
     def to_c(self) -> F.flexi_params:
         return F.flexi_params(N=self.N, Ngeo=self.Ngeo, node_type=self.node_type, riemann=self.riemann,
                               precision=self.precision, bc_exact=self.bc_exact, source=int(self.source),
-                              reserved=0, gamma=self.gamma, Pr=self.Pr, mu=self.mu, Ma=self.Ma)
+                              split_form=self.split_form, gamma=self.gamma, Pr=self.Pr, mu=self.mu, Ma=self.Ma)
 
 
 class Solver:

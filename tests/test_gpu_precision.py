@@ -35,7 +35,7 @@ def test_rhs_fp32_forms_vs_oracle(form, N, nt, riem, nelem):
     Ut = s.rhs(torch.tensor(U0, device=DEV, dtype=torch.float32), 0.0)
     ref, parts = dg.rhs(torch.tensor(U0), 0.0, parts=True)
     scale = (ref.abs() + (parts["vol"] / dg.geo.J.unsqueeze(1)).abs()).transpose(0, 1).reshape(5, -1).norm(dim=1)
-    sig = rounding_sensitivity(dg, torch.tensor(U0), 0.0) * 2.0 ** 29
+    sig = rounding_sensitivity(dg, torch.tensor(U0), 0.0, mesh=mesh) * 2.0 ** 29
     d = (Ut.double().cpu() - ref).transpose(0, 1).reshape(5, -1).norm(dim=1)
     tol = torch.maximum(3e-6 * scale, 20 * sig)
     s.close()
