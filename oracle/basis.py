@@ -16,6 +16,7 @@
   matrix of Eq. discTemp) gives D_hat_ij = -(w_j/w_i) D_ji, the only version
   that differentiates a constant flux to zero together with l_hat.  The tests
   pin that identity.
+* Mortar interpolation and projection matrices (Sec. "Non-conforming meshes").
 """
 from __future__ import annotations
 
@@ -125,6 +126,17 @@ class Basis:
         self.x, self.w, self.D, self.Dhat = t(x), t(w), t(D), t(Dhat)
         self.l_minus, self.l_plus = t(lm), t(lp)
         self.lhat_minus, self.lhat_plus = t(lm / w), t(lp / w)
+        # Mortar operators (Sec. "Non-conforming meshes"), a = 0 lower / 1 upper half
+        # of a big side, whose nodes sit at eta^a_i = (x_i + 2a - 1)/2 in the big
+        # side's coordinate: interpolation I^a_im = l_m(eta^a_i) and the L2
+        # projection P^a_i,alpha = l_i(eta^a_alpha) w_alpha / w_i.  Reading: the
+        # paper's matrix-vector form swaps the superscripts (U^U = I^L U^B); its
+        # element-wise definition, U^L_ij = sum_m U^B_mj l_m(eta^L_i), is used.
+        self.I_mortar, self.P_mortar = [], []
+        for a in (0, 1):
+            V = lagrange_matrix(x, (x + 2 * a - 1) / 2.0)  # V[i, m] = l_m(eta^a_i)
+            self.I_mortar.append(t(V))
+            self.P_mortar.append(t(V.T * w[None, :] / w[:, None]))
 
     def l_side(self, sign: int) -> torch.Tensor:
         return self.l_plus if sign > 0 else self.l_minus

@@ -76,10 +76,10 @@ class Params:
 
 
 class DGSEM:
-    def __init__(self, params: Params, coords: np.ndarray, conn: np.ndarray):
+    def __init__(self, params: Params, coords: np.ndarray, conn: np.ndarray, mortars=None):
         self.p = params
         self.b = Basis(params.N, params.node_type)
-        self.geo = MeshGeometry(self.b, coords, conn)
+        self.geo = MeshGeometry(self.b, coords, conn, mortars)
         self.gas = eq.Gas(params.gamma, params.Pr, params.mu)
         self.K, self.n = self.geo.K, self.b.n
 
@@ -104,6 +104,9 @@ class DGSEM:
         Wf = eq.prim(Uf.movedim(2, -1), gas).movedim(-1, 2)
         UL, UR = geo.master_slave(Uf)
         WL, WR = geo.master_slave(Wf)
+        if len(geo.virt) > 0:  # mortar sides interpolate the solution U; W follows from it
+            WR = WR.clone()
+            WR[geo.virt] = eq.prim(UR[geo.virt].movedim(1, -1), gas).movedim(-1, 1)
         bnd = geo.bnd
         if len(bnd) > 0:
             xb = geo.xface[bnd].movedim(1, -1)

@@ -18,6 +18,12 @@
 * Sides, master/slave and flip (Sec. 5.1): a side is stored once, in the
   side-local frame of its master element; the slave's face data are mapped
   with the orientation code given in the connectivity.
+* Mortars (Sec. "Non-conforming meshes"): every small side of a non-conforming
+  interface is a side of its own whose master is the small element and whose
+  "slave" values are interpolated from the big element's face (I^a along each
+  cut direction of the big side); values returned to the big element are the
+  L2 projection (P^a) of the slave values of its small sides.  Mortar sides
+  carry bc = -2.
 
 Index conventions are those of the ``workloads`` module docstring.
 """
@@ -68,8 +74,11 @@ def orient_index(o: int, N: int) -> np.ndarray:
     return g
 
 
+MORTAR = -(1 << 30)  # connectivity value of a side on a mortar interface
+
+
 class MeshGeometry:
-    def __init__(self, basis: Basis, coords: np.ndarray, conn: np.ndarray):
+    def __init__(self, basis: Basis, coords: np.ndarray, conn: np.ndarray, mortars=None):
         N, n = basis.N, basis.n
         self.basis = basis
         K = coords.shape[0]
@@ -108,17 +117,19 @@ class MeshGeometry:
                 JaL[:, i, nn] = -curl_i
         Ja = interp(JaL.flatten(1, 2), xl, basis.x_np).view(K, 3, 3, n, n, n)
         self.Ja = Ja  # [K, i(contravariant), n(physical), k, j, i]
-        self._build_sides(conn, N)
+        self._build_sides(conn, N, mortars)
         self._face_geometry()
 
     # ------------------------------------------------------------------
-    def _build_sides(self, conn, N):
+    def _build_sides(self, conn, N, mortars):
         K = self.K
         seen = {}
         m_el, m_sd, s_el, s_sd, s_or, bc = [], [], [], [], [], []
         for e in range(K):
             for s in range(6):
                 nb, ns, o = (int(v) for v in conn[e, s])
+                if nb == MORTAR:
+                    continue
                 if nb < 0:
                     m_el.append(e); m_sd.append(s); s_el.append(-1); s_sd.append(-1); s_or.append(0); bc.append(-1 - nb)
                     continue
@@ -132,13 +143,26 @@ class MeshGeometry:
                 else:
                     m_el.append(nb); m_sd.append(ns); s_el.append(e); s_sd.append(s); s_or.append(o)
                 bc.append(-1)
+        # mortar sides: (big element, big side, type, position a, b) per small side
+        self.mortar = []
+        for row in (np.zeros((0, 15), dtype=np.int64) if mortars is None else np.asarray(mortars)):
+            eB, sB, typ = int(row[0]), int(row[1]), int(row[2])
+            for pos in range(4):
+                e2, s2, o2 = (int(v) for v in row[3 + 3 * pos:6 + 3 * pos])
+                if e2 < 0:
+                    continue
+                a = pos % 2 if typ == 3 else (pos if typ == 1 else 0)
+                b = pos // 2 if typ == 3 else (pos if typ == 2 else 0)
+                self.mortar.append((len(m_el), eB, sB, typ, a, b))
+                m_el.append(e2); m_sd.append(s2); s_el.append(-1); s_sd.append(-1); s_or.append(o2); bc.append(-2)
         t = lambda a: torch.tensor(a, dtype=torch.long)
         self.m_el, self.m_sd, self.s_el, self.s_sd = t(m_el), t(m_sd), t(s_el), t(s_sd)
         self.s_or = np.array(s_or)
         self.bc = t(bc)
         self.nsides = len(m_el)
-        self.inner = torch.nonzero(self.bc < 0).flatten()
+        self.inner = torch.nonzero(self.bc == -1).flatten()
         self.bnd = torch.nonzero(self.bc >= 0).flatten()
+        self.virt = torch.nonzero(self.bc == -2).flatten()
         n = N + 1
         # per inner side: gather index slave-local -> master frame, and its inverse
         self.to_master = torch.zeros(self.nsides, n * n, dtype=torch.long)
@@ -186,6 +210,15 @@ class MeshGeometry:
         sl = faces[self.s_el[inn], self.s_sd[inn]].flatten(-2)  # [Si, C, n*n] slave-local
         idx = self.to_master[inn].unsqueeze(1).expand(-1, sl.shape[1], -1)
         S[inn] = torch.gather(sl, 2, idx).view(-1, sl.shape[1], n, n)
+        b = self.basis
+        for sd, eB, sB, typ, a, bq in self.mortar:
+            big = faces[eB, sB]  # [C, q, p] in the big side's frame
+            if typ in (1, 3):  # cut along p: interpolate along p
+                big = torch.einsum("im,cqm->cqi", b.I_mortar[a], big)
+            if typ in (2, 3):  # cut along q
+                big = torch.einsum("jn,cnp->cjp", b.I_mortar[bq], big)
+            # sub-square frame -> frame of the small side (its master)
+            S[sd] = big.flatten(-2)[:, self.to_slave[sd]].view(-1, n, n)
         return M, S
 
     def to_elements(self, master_vals: torch.Tensor, slave_vals: torch.Tensor) -> torch.Tensor:
@@ -200,4 +233,12 @@ class MeshGeometry:
         sv = slave_vals[inn].flatten(-2)
         idx = self.to_slave[inn].unsqueeze(1).expand(-1, C, -1)
         out[self.s_el[inn], self.s_sd[inn]] = torch.gather(sv, 2, idx).view(-1, C, n, n)
+        b = self.basis
+        for sd, eB, sB, typ, a, bq in self.mortar:
+            sub = slave_vals[sd].flatten(-2)[:, self.to_master[sd]].view(C, n, n)  # sub-square frame
+            if typ in (1, 3):
+                sub = torch.einsum("ia,cqa->cqi", b.P_mortar[a], sub)
+            if typ in (2, 3):
+                sub = torch.einsum("jb,cbp->cjp", b.P_mortar[bq], sub)
+            out[eB, sB] = out[eB, sB] + sub
         return out

@@ -20,6 +20,16 @@ Conventions (they define the mesh interface, Sec. 3.1 and Sec. 5.1 of the paper)
   (p, q); p' = N - a if o & 2 else a; q' = N - b if o & 4 else b.
 * conn[e, s] = (neighbour element, neighbour local side, o) or (-1 - bc_id, -1, 0)
   on a boundary.
+* Non-conforming (mortar) interfaces, Sec. 4 "Non-conforming meshes": a big side
+  is cut at the middle of its reference square into two halves along p (type 1),
+  along q (type 2) or into four quarters (type 3).  Sides on such an interface
+  have conn[e, s] = (MORTAR, m, pos), pos = -1 for the big side, and row m of
+  ``mortars`` is (big element, big local side, type, then for pos = 0..3 the
+  small element, its local side and the orientation code o that maps its
+  side-local (p, q) to the node (p', q') of the sub-square in the big side's
+  frame, rescaled to the full index range; -1 where unused).  Position pos is
+  a (type 1), b (type 2) or a + 2 b (type 3), with a = 0 / 1 for the lower /
+  upper half along p and b likewise along q.
 """
 from __future__ import annotations
 
@@ -216,6 +226,171 @@ def box_mesh(nelem=(4, 4, 4), lo=(0.0, 0.0, 0.0), hi=(2 * math.pi,) * 3, Ngeo: i
     mesh = BoxMesh(nelem=tuple(nelem), Ngeo=Ngeo, coords=None, conn=conn, lattice=lattice, frames=frames,
                    lo=lo, hi=hi, mapping=mapping)
     mesh.coords = np.ascontiguousarray(mesh.map_points(xi))
+    return mesh
+
+
+MORTAR = -(1 << 30)  # conn neighbour value of a side on a mortar interface
+
+
+@dataclass
+class NCMesh:
+    """Hexahedra as axis-aligned boxes of a global integer grid (not necessarily
+    conforming), presented as an unstructured mesh with mortar interfaces."""
+
+    box_lo: np.ndarray  # [K, 3] lower corner in grid units
+    box_size: np.ndarray  # [K, 3] extent in grid units
+    dims: np.ndarray  # [3] domain extent in grid units
+    frames: np.ndarray  # [K, 3, 3] local->global signed permutation
+    Ngeo: int
+    coords: np.ndarray
+    conn: np.ndarray
+    mortars: np.ndarray  # [M, 15] int32
+    lo: np.ndarray
+    hi: np.ndarray
+    mapping: str
+
+    @property
+    def K(self) -> int:
+        return self.box_lo.shape[0]
+
+    def map_points(self, xi_local: np.ndarray) -> np.ndarray:
+        eta = np.einsum("kab,...b->k...a", self.frames.astype(float), xi_local)
+        shp = (self.K,) + (1,) * (xi_local.ndim - 1) + (3,)
+        L = self.box_lo.reshape(shp).astype(float)
+        Sz = self.box_size.reshape(shp).astype(float)
+        x = self.lo + (L + (eta + 1.0) / 2.0 * Sz) * (self.hi - self.lo) / self.dims
+        return _apply_mapping(x, self.mapping, self.lo, self.hi)
+
+    def node_coords(self, N: int, node_type: int) -> np.ndarray:
+        r = solution_points(N, node_type)
+        kk, jj, ii = np.meshgrid(r, r, r, indexing="ij")
+        x = self.map_points(np.stack([ii, jj, kk], axis=-1))
+        return np.ascontiguousarray(np.moveaxis(x, -1, 1))
+
+
+def _connect_boxes(box_lo, box_size, dims, frames, periodic, bc_ids):
+    """Face connectivity of a set of boxes: conforming neighbours, boundaries and
+    2:1 mortar interfaces (found geometrically, with periodic wrap)."""
+    K = box_lo.shape[0]
+    faces = {}  # (axis, plane) -> list of (e, s, dirsign, rect)
+    info = {}
+    for e in range(K):
+        R = frames[e]
+        for s in range(6):
+            l, sgn = s // 2, (-1 if s % 2 == 0 else 1)
+            step = R[:, l] * sgn
+            g = int(np.nonzero(step)[0][0])
+            ds = int(step[g])
+            c = int(box_lo[e, g] + (box_size[e, g] if ds > 0 else 0))
+            o1, o2 = [d for d in range(3) if d != g]
+            rect = (int(box_lo[e, o1]), int(box_lo[e, o1] + box_size[e, o1]),
+                    int(box_lo[e, o2]), int(box_lo[e, o2] + box_size[e, o2]))
+            bnd = (c == 0 or c == dims[g]) and not periodic[g]
+            cm = c % dims[g] if periodic[g] else c
+            info[(e, s)] = (g, ds, cm, rect, bnd, c)
+            faces.setdefault((g, cm), []).append((e, s, ds, rect))
+
+    def corners(e, s):
+        """In-plane grid coordinates of the face corners (p, q) in {0,1}^2."""
+        g = info[(e, s)][0]
+        o1, o2 = [d for d in range(3) if d != g]
+        out = {}
+        for p, q in ((0, 0), (1, 0), (0, 1), (1, 1)):
+            xi = _face_corner_xi(s, p, q)
+            X = box_lo[e] + (frames[e] @ xi + 1) / 2.0 * box_size[e]
+            out[(p, q)] = np.array([X[o1], X[o2]])
+        return out
+
+    conn = np.zeros((K, 6, 3), dtype=np.int32)
+    mortars = []
+    for e in range(K):
+        for s in range(6):
+            g, ds, cm, rect, bnd, c = info[(e, s)]
+            if bnd:
+                face = 2 * g + (0 if ds < 0 else 1)
+                conn[e, s] = (-1 - bc_ids[face], -1, 0)
+                continue
+            cands = [(e2, s2, r2) for (e2, s2, ds2, r2) in faces[(g, cm)]
+                     if ds2 == -ds and min(rect[1], r2[1]) > max(rect[0], r2[0])
+                     and min(rect[3], r2[3]) > max(rect[2], r2[2])]
+            area = lambda r: (r[1] - r[0]) * (r[3] - r[2])
+            if len(cands) == 1 and cands[0][2] == rect:
+                e2, s2, _ = cands[0]
+                mine, theirs = corners(e, s), corners(e2, s2)
+                pmap = {pq: next(k for k, v in theirs.items() if np.allclose(v, x)) for pq, x in mine.items()}
+                conn[e, s] = (e2, s2, orientation_code(pmap))
+            elif len(cands) == 1 and area(cands[0][2]) > area(rect):
+                continue  # small side of a mortar: filled from the big side
+            else:
+                if sum(area(r) for _, _, r in cands) != area(rect) or len(cands) not in (2, 4):
+                    raise ValueError("unsupported non-conforming interface")
+                big = corners(e, s)
+                A = big[(0, 0)]
+                up, uq = big[(1, 0)] - A, big[(0, 1)] - A
+                row = [e, s, 0] + [-1] * 12
+                m = len(mortars)
+                for e2, s2, r2 in cands:
+                    sm = corners(e2, s2)
+                    nrm = lambda X: (float((X - A) @ up / (up @ up)), float((X - A) @ uq / (uq @ uq)))
+                    st = [nrm(x) for x in sm.values()]
+                    dp = max(a for a, _ in st) - min(a for a, _ in st)
+                    dq = max(b for _, b in st) - min(b for _, b in st)
+                    typ = {(0.5, 1.0): 1, (1.0, 0.5): 2, (0.5, 0.5): 3}[(round(dp, 6), round(dq, 6))]
+                    ctr = (sum(a for a, _ in st) / 4, sum(b for _, b in st) / 4)
+                    a = int(ctr[0] > 0.5) if dp < 1 else 0
+                    b = int(ctr[1] > 0.5) if dq < 1 else 0
+                    pos = {1: a, 2: b, 3: a + 2 * b}[typ]
+                    pmap = {}
+                    for pq, X in sm.items():
+                        s1, s2v = nrm(X)
+                        pp = int(round(2 * s1 - a)) if dp < 1 else int(round(s1))
+                        qq = int(round(2 * s2v - b)) if dq < 1 else int(round(s2v))
+                        pmap[pq] = (pp, qq)
+                    row[2] = typ
+                    row[3 + 3 * pos:6 + 3 * pos] = [e2, s2, orientation_code(pmap)]
+                    conn[e2, s2] = (MORTAR, m, pos)
+                conn[e, s] = (MORTAR, m, -1)
+                mortars.append(row)
+    return conn, np.array(mortars, dtype=np.int32).reshape(-1, 15)
+
+
+def mortar_box_mesh(ny: int = 2, nz: int = 2, nx: int = 1, refine=(1, 2, 2), lo=(-1.0,) * 3, hi=(1.0,) * 3,
+                    Ngeo: int = 1, periodic=(True, True, True), mapping: str = "cartesian",
+                    reorient_seed=None, bc_ids=None) -> NCMesh:
+    """Two blocks of equal width in x: the left one of nx * ny * nz elements, the
+    right one refined by refine = (rx, ry, rz) in {1, 2}^3 (ry * rz > 1).  The
+    interface at the middle of the box (and, with periodic x, the one at its
+    ends) is non-conforming: type 3 mortars for ry = rz = 2, halves otherwise.
+    With the "sine" mapping on [-1, 1]^3 both interfaces lie on planes where the
+    bump vanishes, so big and small faces are the same flat patches."""
+    rx, ry, rz = refine
+    cl, fl = [], []
+    for c in range(nz):
+        for b in range(ny):
+            for a in range(nx):
+                cl.append(((2 * a, 2 * b, 2 * c), (2, 2, 2)))
+    sx, sy, sz = 2 // rx, 2 // ry, 2 // rz
+    for c in range(nz * rz):
+        for b in range(ny * ry):
+            for a in range(nx * rx):
+                fl.append(((2 * nx + sx * a, sy * b, sz * c), (sx, sy, sz)))
+    boxes = cl + fl
+    box_lo = np.array([b[0] for b in boxes], dtype=np.int64)
+    box_size = np.array([b[1] for b in boxes], dtype=np.int64)
+    dims = np.array([4 * nx, 2 * ny, 2 * nz], dtype=np.int64)
+    K = len(boxes)
+    rots = cube_rotations()
+    if reorient_seed is None:
+        frames = np.tile(np.eye(3, dtype=np.int64), (K, 1, 1))
+    else:
+        rng = np.random.default_rng(reorient_seed)
+        frames = np.stack([rots[rng.integers(len(rots))] for _ in range(K)])
+    conn, mortars = _connect_boxes(box_lo, box_size, dims, frames, periodic, bc_ids if bc_ids else [0] * 6)
+    r = lobatto_points(Ngeo)
+    kk, jj, ii = np.meshgrid(r, r, r, indexing="ij")
+    mesh = NCMesh(box_lo=box_lo, box_size=box_size, dims=dims, frames=frames, Ngeo=Ngeo, coords=None, conn=conn,
+                  mortars=mortars, lo=np.asarray(lo, float), hi=np.asarray(hi, float), mapping=mapping)
+    mesh.coords = np.ascontiguousarray(mesh.map_points(np.stack([ii, jj, kk], axis=-1)))
     return mesh
 
 
