@@ -435,6 +435,10 @@ def extras(args, s64, U0, mesh, dt, dev, F, wl, Solver, SolverConfig, torch, np)
     except Exception as exc:
         out["lobatto"] = {"error": repr(exc)}
     try:
+        out["mortar"] = mortar_pid(dt, dev, F, wl, Solver, SolverConfig, torch)
+    except Exception as exc:
+        out["mortar"] = {"error": repr(exc)}
+    try:
         out["adjoint"] = adjoint_ratio(dev, F, wl, Solver, SolverConfig, torch)
     except Exception as exc:
         out["adjoint"] = {"error": repr(exc)}
@@ -475,6 +479,43 @@ def lobatto_pid(mesh, dt, dev, F, wl, Solver, SolverConfig, torch):
         finally:
             s.close()
     return res
+
+
+def mortar_pid(dt, dev, F, wl, Solver, SolverConfig, torch):
+    """Taylor-Green step (N = 7 Gauss, HLLC, FP64) on a non-conforming periodic
+    [0, 2 pi]^3 mesh: left half 4 x 8 x 8 elements, right half refined 2:1 in
+    every direction (8 x 16 x 16), type-3 mortars at both interfaces (128 big
+    sides); PID and the share of the mortar kernels."""
+    import math
+
+    m = wl.mortar_box_mesh(nx=4, ny=8, nz=8, refine=(2, 2, 2), lo=(0.0,) * 3, hi=(2 * math.pi,) * 3)
+    s = Solver(SolverConfig(N=7, riemann=F.RIEMANN_HLLC, precision=F.FP64), m.coords, m.conn, device=dev,
+               mortars=m.mortars)
+    try:
+        U = torch.tensor(wl.taylor_green(m.node_coords(7, 0)), device=dev)
+        dU = torch.zeros_like(U)
+        dtm = 0.5 * dt  # the fine half has half the element width
+        for _ in range(3):
+            s.step(U, dU, 0.0, dtm)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for k in range(10):
+            s.step(U, dU, k * dtm, dtm)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1)
+        F.flexi_profile(s.ctx, True)
+        for k in range(2):
+            s.step(U, dU, k * dtm, dtm)
+        torch.cuda.synchronize(dev)
+        kt = F.flexi_kernel_times(s.ctx, reset=True)
+        F.flexi_profile(s.ctx, False)
+        tot = sum(v[0] for v in kt.values())
+        return {"elements": m.K, "mortars": int(len(m.mortars)), "pid": ms * 1e6 / (10 * NSTAGES * s.query(F.Q_DOF)),
+                "steps": 10, "mortar_kernel_share": kt["other"][0] / tot if tot > 0 else None}
+    finally:
+        s.close()
 
 
 def adjoint_ratio(dev, F, wl, Solver, SolverConfig, torch):

@@ -101,6 +101,28 @@ typedef struct {
 flexi_status flexi_mesh_init(flexi_ctx **out, const flexi_params *p, int K, const double *coords,
                              const int32_t *conn, void *stream);
 
+/* Non-conforming meshes (Sec. "Non-conforming meshes", mortar method): a big side
+ * is cut at the middle of its reference square into two halves along its first
+ * face coordinate p (type 1), along q (type 2) or into four quarters (type 3).
+ *   conn:    as for flexi_mesh_init, except that every side on such an interface
+ *            has (FLEXI_CONN_MORTAR, m, pos): m the mortar row, pos = -1 for the
+ *            big side, else the small side's position.
+ *   mortars: HOST pointer, int32 [M][15]: (big element, big local side, type,
+ *            then for pos = 0..3: small element, small local side, orientation
+ *            code mapping the small side's (p, q) to the node (p', q') of its
+ *            sub-square of the big side, rescaled to 0..N; -1 -1 -1 where the
+ *            type has only two positions).  pos = a (type 1), b (type 2) or
+ *            a + 2b (type 3), a / b = 0 for the lower, 1 for the upper half
+ *            along p / q of the big side's frame.
+ * Per stage the big element's solution U and lifted gradients are interpolated
+ * to the small sides (I^L, I^U), the numerical and BR1 lifting fluxes are
+ * computed there and L2-projected back (P^L, P^U).  Returns FLEXI_EMESH for
+ * inconsistent mortar rows; otherwise as flexi_mesh_init.  The discrete adjoint
+ * does not support mortars (FLEXI_EUNSUPPORTED). */
+#define FLEXI_CONN_MORTAR (-1073741824)
+flexi_status flexi_mesh_init_mortar(flexi_ctx **out, const flexi_params *p, int K, const double *coords,
+                                    const int32_t *conn, int M, const int32_t *mortars, void *stream);
+
 /* Ut = L(U, t): the semi-discrete right-hand side, Eq. semiDiscrete with the
  * BR1 gradients of Eq. discreteGradient (steps: prolongation, lifting, face
  * fluxes, volume integral, surface integral, 1/J scaling).  U, Ut: device. */

@@ -23,6 +23,14 @@ struct Ops {
   real DT[MAXN * MAXN];  // DT[a * n + i] = D[i][a]  (strong-form derivative, split form only)
 };
 
+// mortar operators (Sec. "Non-conforming meshes"), a = 0 lower / 1 upper half:
+// I[a][i * n + m] = l_m((x_i + 2a - 1)/2), P[a][i * n + al] = l_i((x_al + 2a - 1)/2) w_al / w_i
+template <typename real>
+struct MortarOps {
+  real I[2][MAXN * MAXN];
+  real P[2][MAXN * MAXN];
+};
+
 template <typename real>
 struct Phys {
   real gamma, gm1, inv_gm1, mu, lam_th;  // lam_th = mu gamma / ((gamma-1) Pr)

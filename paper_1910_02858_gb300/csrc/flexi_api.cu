@@ -49,6 +49,9 @@ struct flexi_ctx {
   void* adj_scratch = nullptr;
   Ops<double> ops64{};
   Ops<float> ops32{};
+  MortarOps<double> mops64{};
+  MortarOps<float> mops32{};
+  int nMortar = 0;
   Phys<double> ph64{};
   Phys<float> ph32{};
   SourceParams src{};
@@ -124,6 +127,12 @@ const Ops<double>& ops_of<double>(const flexi_ctx* c) { return c->ops64; }
 template <>
 const Ops<float>& ops_of<float>(const flexi_ctx* c) { return c->ops32; }
 template <typename real>
+const MortarOps<real>& mo_of(const flexi_ctx* c);
+template <>
+const MortarOps<double>& mo_of<double>(const flexi_ctx* c) { return c->mops64; }
+template <>
+const MortarOps<float>& mo_of<float>(const flexi_ctx* c) { return c->mops32; }
+template <typename real>
 const Phys<real>& ph_of(const flexi_ctx* c);
 template <>
 const Phys<double>& ph_of<double>(const flexi_ctx* c) { return c->ph64; }
@@ -143,13 +152,25 @@ flexi_status stage_front(flexi_ctx* c, const real* U, double t, bool prolong, in
     Prof pr(c, KC_BC, st);
     CK(launch_bc<real>(c->m, t, ph, st));
   }
+  if (c->nMortar > 0) {
+    Prof pr(c, KC_OTHER, st);
+    CK(launch_mortar_state<real>(c->m, mo_of<real>(c), ph, st));
+  }
   {
     Prof pr(c, KC_LIFTVOL, st);
     CK(launch_lift_vol<real>(c->m, U, ops, ph, store_grad, st));
   }
+  if (c->nMortar > 0) {
+    Prof pr(c, KC_OTHER, st);
+    CK(launch_mortar_grad<real>(c->m, mo_of<real>(c), ph, st));
+  }
   {
     Prof pr(c, KC_FACE, st);
     CK(launch_face<real>(c->m, ph, st));
+  }
+  if (c->nMortar > 0) {
+    Prof pr(c, KC_OTHER, st);
+    CK(launch_mortar_flux<real>(c->m, mo_of<real>(c), st));
   }
   return FLEXI_OK;
 }
@@ -228,8 +249,23 @@ bool orient_inverse(int o, int oinv, int N) {
   return true;
 }
 
+template <typename real>
+void fill_mortar_ops(MortarOps<real>& o, const std::vector<double>& x, const std::vector<double>& w, int n) {
+  std::memset(&o, 0, sizeof(o));
+  for (int a = 0; a < 2; ++a) {
+    std::vector<double> eta(n);
+    for (int i = 0; i < n; ++i) eta[i] = 0.5 * (x[i] + 2.0 * a - 1.0);
+    const std::vector<double> V = host::interp_matrix(x, eta);  // V[i * n + m] = l_m(eta_i)
+    for (int i = 0; i < n; ++i)
+      for (int m = 0; m < n; ++m) {
+        o.I[a][i * n + m] = (real)V[i * n + m];
+        o.P[a][i * n + m] = (real)(V[m * n + i] * w[m] / w[i]);  // l_i(eta_m) w_m / w_i
+      }
+  }
+}
+
 flexi_status mesh_init_impl(flexi_ctx* c, const flexi_params* p, int K, const double* coords, const int32_t* conn,
-                            cudaStream_t st) {
+                            int M, const int32_t* mortars, cudaStream_t st) {
   c->p = *p;
   c->K = K;
   c->N = p->N;
@@ -241,13 +277,43 @@ flexi_status mesh_init_impl(flexi_ctx* c, const flexi_params* p, int K, const do
   const int N = c->N, n = c->n, n3 = c->n3, n2 = c->n2;
   const int ng = p->Ngeo + 1, ng3 = ng * ng * ng;
 
-  // ---- sides (Sec. 5.1): boundary sides first, then inner sides; master = smaller (elem, side) key
+  // ---- mortar rows: (big element, big side, type, (small element, side, o) x 4)
+  int nMortarSides = 0;
+  for (int m = 0; m < M; ++m) {
+    const int32_t* r = mortars + 15 * m;
+    const int eB = r[0], sB = r[1], typ = r[2];
+    if (eB < 0 || eB >= K || sB < 0 || sB > 5 || typ < 1 || typ > 3) return FLEXI_EMESH;
+    const int* cb = conn + (eB * 6 + sB) * 3;
+    if (cb[0] != FLEXI_CONN_MORTAR || cb[1] != m || cb[2] != -1) return FLEXI_EMESH;
+    ++nMortarSides;
+    for (int pos = 0; pos < 4; ++pos) {
+      const int e2 = r[3 + 3 * pos], s2 = r[4 + 3 * pos], o2 = r[5 + 3 * pos];
+      if (typ < 3 && pos >= 2) {
+        if (e2 != -1) return FLEXI_EMESH;
+        continue;
+      }
+      if (e2 < 0 || e2 >= K || s2 < 0 || s2 > 5 || o2 < 0 || o2 > 7) return FLEXI_EMESH;
+      const int* cs = conn + (e2 * 6 + s2) * 3;
+      if (cs[0] != FLEXI_CONN_MORTAR || cs[1] != m || cs[2] != pos) return FLEXI_EMESH;
+      ++nMortarSides;
+    }
+  }
+
+  // ---- sides (Sec. 5.1): boundary sides first, then inner sides (master = smaller
+  // (elem, side) key), then one side per small face of a mortar (master = the small
+  // element), then the big sides of the mortars
   std::vector<int> es(K * 6, -1);
   std::vector<int> sideMaster;
   std::vector<int> bnd_pairs, inner_pairs;  // (e, s)
+  int nMarked = 0;
   for (int e = 0; e < K; ++e)
     for (int s = 0; s < 6; ++s) {
       const int nb = conn[(e * 6 + s) * 3 + 0], ns = conn[(e * 6 + s) * 3 + 1], o = conn[(e * 6 + s) * 3 + 2];
+      if (nb == FLEXI_CONN_MORTAR) {
+        if (ns < 0 || ns >= M) return FLEXI_EMESH;
+        ++nMarked;
+        continue;
+      }
       if (nb < 0) {
         bnd_pairs.push_back(e * 6 + s);
         continue;
@@ -257,8 +323,11 @@ flexi_status mesh_init_impl(flexi_ctx* c, const flexi_params* p, int K, const do
       if (bnb != e || bns != s || !orient_inverse(o, bo, N)) return FLEXI_EMESH;
       if (e * 6 + s < nb * 6 + ns) inner_pairs.push_back(e * 6 + s);
     }
+  if (nMarked != nMortarSides) return FLEXI_EMESH;
+  const int nV = nMortarSides - M;
   c->nBC = (int)bnd_pairs.size();
-  c->S = c->nBC + (int)inner_pairs.size();
+  c->nMortar = M;
+  c->S = c->nBC + (int)inner_pairs.size() + nV + M;
   sideMaster.resize(2 * c->S);
   int sid = 0;
   for (int key : bnd_pairs) {
@@ -277,6 +346,40 @@ flexi_status mesh_init_impl(flexi_ctx* c, const flexi_params* p, int K, const do
     sideMaster[2 * sid + 1] = s;
     ++sid;
   }
+  const int vbase = sid, bigBase = sid + nV;
+  std::vector<int> mvirt((size_t)std::max(nV, 1) * 4, 0), mbig((size_t)std::max(M, 1) * 8, -1);
+  for (int m = 0; m < M; ++m) {
+    const int32_t* r = mortars + 15 * m;
+    const int typ = r[2];
+    mbig[m * 8] = typ;
+    for (int pos = 0; pos < (typ == 3 ? 4 : 2); ++pos) {
+      const int e2 = r[3 + 3 * pos], s2 = r[4 + 3 * pos], o2 = r[5 + 3 * pos];
+      int oinv = -1;
+      for (int t = 0; t < 8 && oinv < 0; ++t)
+        if (orient_inverse(o2, t, N)) oinv = t;
+      const int a = typ == 3 ? (pos & 1) : (typ == 1 ? pos : 0);
+      const int b = typ == 3 ? (pos >> 1) : (typ == 2 ? pos : 0);
+      int* mv = &mvirt[(size_t)(sid - vbase) * 4];
+      mv[0] = bigBase + m;
+      mv[1] = typ | (a << 2) | (b << 3);
+      mv[2] = o2;
+      mv[3] = oinv;
+      mbig[m * 8 + 1 + pos] = sid;
+      if (es[e2 * 6 + s2] != -1) return FLEXI_EMESH;
+      es[e2 * 6 + s2] = (sid << 4);
+      sideMaster[2 * sid] = e2;
+      sideMaster[2 * sid + 1] = s2;
+      ++sid;
+    }
+  }
+  for (int m = 0; m < M; ++m) {
+    const int eB = mortars[15 * m], sB = mortars[15 * m + 1];
+    if (es[eB * 6 + sB] != -1) return FLEXI_EMESH;
+    es[eB * 6 + sB] = (sid << 4);
+    sideMaster[2 * sid] = eB;
+    sideMaster[2 * sid + 1] = sB;
+    ++sid;
+  }
   for (int v : es)
     if (v < 0) return FLEXI_EMESH;
   const int S = c->S;
@@ -292,6 +395,8 @@ flexi_status mesh_init_impl(flexi_ctx* c, const flexi_params* p, int K, const do
   const std::vector<double> lmv = host::interp_matrix(xs, {-1.0}), lpv = host::interp_matrix(xs, {1.0});
   fill_ops<double>(c->ops64, Ds, ws, lmv, lpv, n);
   fill_ops<float>(c->ops32, Ds, ws, lmv, lpv, n);
+  fill_mortar_ops<double>(c->mops64, xs, ws, n);
+  fill_mortar_ops<float>(c->mops32, xs, ws, n);
   fill_phys<double>(c->ph64, *p);
   fill_phys<float>(c->ph32, *p);
   c->src.on = p->source;
@@ -407,6 +512,22 @@ flexi_status mesh_init_impl(flexi_ctx* c, const flexi_params* p, int K, const do
 
   // ---- arithmetic-form copies and scratch
   c->m.K = K; c->m.S = S; c->m.nBC = c->nBC; c->m.N = N; c->m.n = n;
+  c->m.Sface = S - M;
+  c->m.vbase = vbase;
+  c->m.nV = nV;
+  c->m.nBig = M;
+  if (M > 0) {
+    int *dmv, *dmb;
+    AL(dmv, mvirt.size());
+    AL(dmb, mbig.size());
+    CK(cudaMemcpy(dmv, mvirt.data(), mvirt.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(dmb, mbig.data(), mbig.size() * sizeof(int), cudaMemcpyHostToDevice));
+    c->m.mvirt = dmv;
+    c->m.mbig = dmb;
+    unsigned char* qb;
+    AL(qb, (size_t)M * 15 * n2 * c->rs);
+    c->m.QB = qb;
+  }
   c->m.elemSide = c->elemSide;
   c->m.xbc = c->xbc;
   c->m.xsol = c->xsol;
@@ -559,7 +680,13 @@ void flexi_destroy(flexi_ctx* c) {
 
 flexi_status flexi_mesh_init(flexi_ctx** out, const flexi_params* p, int K, const double* coords,
                              const int32_t* conn, void* stream) {
+  return flexi_mesh_init_mortar(out, p, K, coords, conn, 0, nullptr, stream);
+}
+
+flexi_status flexi_mesh_init_mortar(flexi_ctx** out, const flexi_params* p, int K, const double* coords,
+                                    const int32_t* conn, int M, const int32_t* mortars, void* stream) {
   if (out == nullptr || p == nullptr || coords == nullptr || conn == nullptr || K <= 0) return FLEXI_EINVAL;
+  if (M < 0 || (M > 0 && mortars == nullptr)) return FLEXI_EINVAL;
   *out = nullptr;
   if (p->N < 1 || p->N > 7) return p->N > 7 ? FLEXI_EUNSUPPORTED : FLEXI_EINVAL;
   if (p->Ngeo < 1 || p->Ngeo > p->N) return FLEXI_EINVAL;
@@ -574,7 +701,7 @@ flexi_status flexi_mesh_init(flexi_ctx** out, const flexi_params* p, int K, cons
   if ((long long)K * 6 >= (1LL << 27)) return FLEXI_EUNSUPPORTED;
   flexi_ctx* c = new (std::nothrow) flexi_ctx();
   if (c == nullptr) return FLEXI_ENOMEM;
-  const flexi_status s = mesh_init_impl(c, p, K, coords, conn, (cudaStream_t)stream);
+  const flexi_status s = mesh_init_impl(c, p, K, coords, conn, M, mortars, (cudaStream_t)stream);
   if (s != FLEXI_OK) {
     flexi_destroy(c);
     return s;
@@ -606,8 +733,9 @@ flexi_status flexi_rk_step_stages(flexi_ctx* c, void* U, void* dU, double t, dou
 }
 
 static bool adjoint_supported(const flexi_ctx* c) {
-  return c->nBC == 0 && (c->p.riemann == FLEXI_RIEMANN_ROE || c->p.riemann == FLEXI_RIEMANN_ROE_SMOOTH) &&
-         !c->p.source && c->p.split_form == FLEXI_SPLIT_STANDARD;
+  return c->nBC == 0 && c->nMortar == 0 &&
+         (c->p.riemann == FLEXI_RIEMANN_ROE || c->p.riemann == FLEXI_RIEMANN_ROE_SMOOTH) && !c->p.source &&
+         c->p.split_form == FLEXI_SPLIT_STANDARD;
 }
 
 flexi_status flexi_adjoint_step(flexi_ctx* c, const void* U_stages, void* lamU, void* lam_dU, double t, double dt,

@@ -243,8 +243,8 @@ template <typename real, int n, int SW, bool LGL, bool SPLIT = false>
 __global__ void __launch_bounds__(Cfg<n>::T) k_lift_vol(
     const real* __restrict__ U, const real* __restrict__ Ja, const real* __restrict__ sJ,
     const real* __restrict__ Wf, const real* __restrict__ fgeo, const int* __restrict__ elemSide,
-    real* __restrict__ Gf, real* __restrict__ Utv, real* __restrict__ Gvol, int K, int S, Ops<real> ops,
-    Phys<real> ph) {
+    real* __restrict__ Gf, real* __restrict__ Utv, real* __restrict__ Gvol, int K, int S, int bigBase,
+    const real* __restrict__ QB, Ops<real> ops, Phys<real> ph) {
   using C = Cfg<n>;
   constexpr int n2 = C::n2, n3 = C::n3, NE = C::NE, T = C::T, n3p = C::n3p;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -287,7 +287,8 @@ __global__ void __launch_bounds__(Cfg<n>::T) k_lift_vol(
   BFrag<SW> bfr;
   if constexpr (SW != 0) bfr = make_bfrag<n, SW>(reinterpret_cast<const float*>(sOp), tid & 31);
 
-  // BR1 surface terms: Q = U* n_d s_hat with the element's outward normal
+  // BR1 surface terms: Q = U* n_d s_hat with the element's outward normal (big
+  // sides of mortars: the projected lifting flux of their small sides)
   for (int it = tid; it < NE * 6 * n2; it += T) {
     const int el2 = it / (6 * n2);
     const int r = it - el2 * 6 * n2;
@@ -296,6 +297,13 @@ __global__ void __launch_bounds__(Cfg<n>::T) k_lift_vol(
     const int es = sES[el2 * 6 + s];
     const int side = es_side(es);
     const int mpq = orient_pq(es_orient(es), n - 1, pq % n, pq / n);
+    if (side >= bigBase) {
+      const real* qb = QB + ((size_t)(side - bigBase) * 15) * n2 + mpq;
+      real* Q = sQ + ((el2 * 6 + s) * 15) * n2 + pq;
+#pragma unroll
+      for (int c = 0; c < 15; ++c) Q[c * n2] = qb[c * n2];
+      continue;
+    }
     const real* w0 = Wf + ((size_t)side * NV) * n2 + mpq;
     const real* w1 = Wf + ((size_t)(S + side) * NV) * n2 + mpq;
     const real* g = fgeo + ((size_t)side * 4) * n2 + mpq;
@@ -763,7 +771,9 @@ static cudaError_t lift_vol_n(const DevMesh& m, const real* U, const Ops<real>& 
   k_lift_vol<real, n, SW, LGL, SPLIT><<<grid, C::T, smem, st>>>(U, (const real*)m.Ja, (const real*)m.sJ,
                                                          (const real*)m.Wf, (const real*)m.fgeo, m.elemSide,
                                                          (real*)m.Gf, (real*)m.Utv,
-                                                         store_grad ? (real*)m.Gvol : nullptr, m.K, m.S, ops, ph);
+                                                         store_grad ? (real*)m.Gvol : nullptr, m.K, m.S,
+                                                         m.Sface, (const real*)m.QB,
+                                                         ops, ph);
   return cudaGetLastError();
 }
 
@@ -789,7 +799,7 @@ cudaError_t launch_lift_vol(const DevMesh& m, const real* U, const Ops<real>& op
 
 template <typename real>
 cudaError_t launch_face(const DevMesh& m, const Phys<real>& ph, cudaStream_t st) {
-  const int tot = m.S * m.n * m.n;
+  const int tot = m.Sface * m.n * m.n;  // big sides of mortars get their flux by projection
   FLEXI_DISPATCH_N(m.n, (k_face<real, NN><<<(tot + 127) / 128, 128, 0, st>>>(
                             (const real*)m.Wf, (const real*)m.Gf, (const real*)m.fgeo, (real*)m.Ff, m.S, m.nBC, ph)));
   return cudaGetLastError();

@@ -25,6 +25,13 @@ struct DevMesh {
   void* Ff = nullptr;          // [S][5][n^2] numerical flux f* s_hat in the master normal
   void* Utv = nullptr;         // [K][5][n^3] volume-integral part of U_t
   void* Gvol = nullptr;        // [K][15][n^3] volume gradients (adjoint only)
+  // mortars: sides are [boundary][inner][virtual small sides][big sides]
+  int Sface = 0;               // sides with a numerical flux (all but the big sides)
+  int vbase = 0, nV = 0;       // first virtual side and their count
+  int nBig = 0;                // big sides, ids Sface .. S-1
+  const int* mvirt = nullptr;  // [nV] int4 (big side, type | a<<2 | b<<3, o, oinv)
+  const int* mbig = nullptr;   // [nBig][8] (type, virtual side of position 0..3 or -1)
+  void* QB = nullptr;          // [nBig][15][n^2] BR1 lifting flux of the big element
   unsigned* status = nullptr;  // device status word (bit 0: non-physical face state)
 };
 
@@ -49,6 +56,13 @@ cudaError_t launch_lift_vol(const DevMesh& m, const real* U, const Ops<real>& op
                             int store_grad, cudaStream_t st);
 template <typename real>
 cudaError_t launch_face(const DevMesh& m, const Phys<real>& ph, cudaStream_t st);
+// mortars: face states + lifting flux of big sides; gradients; projected fluxes
+template <typename real>
+cudaError_t launch_mortar_state(const DevMesh& m, const MortarOps<real>& mo, const Phys<real>& ph, cudaStream_t st);
+template <typename real>
+cudaError_t launch_mortar_grad(const DevMesh& m, const MortarOps<real>& mo, const Phys<real>& ph, cudaStream_t st);
+template <typename real>
+cudaError_t launch_mortar_flux(const DevMesh& m, const MortarOps<real>& mo, cudaStream_t st);
 // mode 0: Ut = L(U); mode 1: RK stage update of U, dU in place
 template <typename real>
 cudaError_t launch_surf(const DevMesh& m, int mode, real* U, real* dU, real* Ut, const RkStage<real>& rk,

@@ -20,11 +20,12 @@ RIEMANN_ROE, RIEMANN_HLLC, RIEMANN_ROE_SMOOTH, RIEMANN_RUSANOV = 0, 1, 2, 3
 FP64, FP32, FP32_TF32, FP32_BF16 = 0, 1, 2, 3
 EXACT_TGV, EXACT_FREESTREAM, EXACT_MANUFACTURED = 0, 1, 2
 SPLIT_STANDARD, SPLIT_KEP = 0, 1
+CONN_MORTAR = -(1 << 30)
 Q_K, Q_N, Q_NSIDES, Q_NBCSIDES, Q_DOF, Q_BYTES_PER_STAGE, Q_FLOPS_PER_STAGE, Q_STATUS, Q_DEVICE_BYTES, Q_PRECISION = range(10)
 KERNEL_CLASSES = ["lift_vol", "face", "surf_rk", "prolong", "bc", "adjoint", "reduce", "other"]
 
 # every entry point declared in include/flexi.h
-EXPORTS = ["flexi_mesh_init", "flexi_rhs", "flexi_rk_step", "flexi_rk_step_stages", "flexi_adjoint_step",
+EXPORTS = ["flexi_mesh_init", "flexi_mesh_init_mortar", "flexi_rhs", "flexi_rk_step", "flexi_rk_step_stages", "flexi_adjoint_step",
            "flexi_rhs_adjoint", "flexi_rk_run_host", "flexi_reduce", "flexi_reduce_noalloc", "flexi_query",
            "flexi_profile", "flexi_kernel_times", "flexi_strerror", "flexi_destroy"]
 NOALLOC_MAX_ELEMENTS = 65536
@@ -56,6 +57,7 @@ def lib() -> ctypes.CDLL:
         L = ctypes.CDLL(LIB_PATH)
         vp, d, i, i64p = ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)
         L.flexi_mesh_init.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(flexi_params), i, vp, vp, vp]
+        L.flexi_mesh_init_mortar.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(flexi_params), i, vp, vp, i, vp, vp]
         L.flexi_rhs.argtypes = [vp, vp, vp, d, vp]
         L.flexi_rk_step.argtypes = [vp, vp, vp, d, d, vp]
         L.flexi_rk_step_stages.argtypes = [vp, vp, vp, d, d, vp, vp]
@@ -103,6 +105,19 @@ def flexi_mesh_init(params: flexi_params, coords: np.ndarray, conn: np.ndarray, 
     check(lib().flexi_mesh_init(ctypes.byref(ctx), ctypes.byref(params), int(coords.shape[0]),
                                 coords.ctypes.data_as(ctypes.c_void_p), conn.ctypes.data_as(ctypes.c_void_p),
                                 _stream(stream)), "flexi_mesh_init")
+    return ctx
+
+
+def flexi_mesh_init_mortar(params: flexi_params, coords: np.ndarray, conn: np.ndarray, mortars: np.ndarray,
+                           stream=None) -> ctypes.c_void_p:
+    coords = np.ascontiguousarray(coords, dtype=np.float64)
+    conn = np.ascontiguousarray(conn, dtype=np.int32)
+    mortars = np.ascontiguousarray(mortars, dtype=np.int32).reshape(-1, 15)
+    ctx = ctypes.c_void_p()
+    check(lib().flexi_mesh_init_mortar(ctypes.byref(ctx), ctypes.byref(params), int(coords.shape[0]),
+                                       coords.ctypes.data_as(ctypes.c_void_p), conn.ctypes.data_as(ctypes.c_void_p),
+                                       int(mortars.shape[0]), mortars.ctypes.data_as(ctypes.c_void_p),
+                                       _stream(stream)), "flexi_mesh_init_mortar")
     return ctx
 
 

@@ -34,11 +34,15 @@ class SolverConfig:
 
 
 class Solver:
-    def __init__(self, cfg: SolverConfig, coords: np.ndarray, conn: np.ndarray, device="cuda:0"):
+    def __init__(self, cfg: SolverConfig, coords: np.ndarray, conn: np.ndarray, device="cuda:0", mortars=None):
         self.cfg = cfg
         self.device = torch.device(device)
         with torch.cuda.device(self.device):
-            self.ctx = F.flexi_mesh_init(cfg.to_c(), coords, conn, torch.cuda.current_stream(self.device))
+            stream = torch.cuda.current_stream(self.device)
+            if mortars is not None and len(mortars) > 0:
+                self.ctx = F.flexi_mesh_init_mortar(cfg.to_c(), coords, conn, mortars, stream)
+            else:
+                self.ctx = F.flexi_mesh_init(cfg.to_c(), coords, conn, stream)
         self.K = F.flexi_query(self.ctx, F.Q_K)
         self.n = cfg.N + 1
         self.dtype = torch.float64 if cfg.precision == F.FP64 else torch.float32
