@@ -252,7 +252,8 @@ __global__ void __launch_bounds__(Cfg<n>::T) k_lift_vol(
   constexpr int nout = (sizeof(real) == 8 && SW == 0) ? 0 : NE * NV * n3p;
   real* sOut = sbuf + NE * 15 * n3p;               // [NE][5][n3p]  sweep results (not for FP64)
   real* sQ = sOut + nout;                          // [NE][6][15][n2]  (v*3+d)
-  real* sOp = sQ + NE * 6 * 15 * n2;               // DhatT, lm, lp, lhm, lhp (+ DT with SPLIT)
+  real* sO = sQ + NE * 6 * 15 * n2;  // SPLIT, FP64: [NE][3][5][n3p] two-point sums per direction
+  real* sOp = sO + ((SPLIT && sizeof(real) == 8) ? NE * 3 * NV * n3p : 0);  // DhatT, lm, lp, lhm, lhp (+ DT)
   int* sES = reinterpret_cast<int*>(sOp + n2 + 4 * n + (SPLIT ? n2 : 0));
   static_assert(!SPLIT || (LGL && SW == 0), "the split form is built on Gauss-Lobatto nodes with CUDA-core sweeps");
 
@@ -476,37 +477,115 @@ __global__ void __launch_bounds__(Cfg<n>::T) k_lift_vol(
 #pragma unroll
     for (int c = 0; c < 9; ++c) myb[(6 + c) * n3p + pn] = jac[c];
     __syncthreads();
-    const real* sD = sOp + n2 + 4 * n;  // DT[a * n + i] = D[i][a]
+    if constexpr (sizeof(real) == 4) {
+      // FP32: thread per node, all n pairs of each of its three lines (keeps every
+      // thread busy; the FP32 pipes are not the limit)
+      const real* sD = sOp + n2 + 4 * n;  // DT[a * n + i] = D[i][a]
+#pragma unroll
+      for (int l = 0; l < 3; ++l) {
+        const int il = l == 0 ? i : (l == 1 ? j : k);
+        const real J0 = jac[l * 3], J1 = jac[l * 3 + 1], J2 = jac[l * 3 + 2];
+        real sm[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) sm[v] = real(0);
+#pragma unroll
+        for (int a = 0; a < n; ++a) {
+          const int pa = l == 0 ? pidx<n>(a, j, k) : (l == 1 ? pidx<n>(i, a, k) : pidx<n>(i, j, a));
+          const real* f = myb + pa;
+          const real rs = W[0] + f[0], us = W[1] + f[n3p], vs = W[2] + f[2 * n3p], ws = W[3] + f[3 * n3p];
+          const real ps = W[4] + f[4 * n3p], Hs = H + f[5 * n3p];
+          const real j0 = J0 + f[(6 + 3 * l) * n3p], j1 = J1 + f[(7 + 3 * l) * n3p], j2 = J2 + f[(8 + 3 * l) * n3p];
+          const real m = real(0.125) * rs * (us * j0 + vs * j1 + ws * j2);
+          const real d = sD[a * n + il];
+          const real dm = d * m, dp = real(0.5) * d * ps;
+          sm[0] += dm;
+          sm[1] += dm * us + dp * j0;
+          sm[2] += dm * vs + dp * j1;
+          sm[3] += dm * ws + dp * j2;
+          sm[4] += dm * Hs;
+        }
+        acc[0] += real(2) * sm[0];
+#pragma unroll
+        for (int v = 1; v < NV; ++v) acc[v] += sm[v];
+      }
+    } else {
+      // One thread per (direction l, line): F# is symmetric, so every pair (i, a),
+      // i < a, of the line is evaluated once and gives D_ia F# to node i and
+      // D_ai F# to node a.  Diagonal terms: D_ii = 0 at the interior Gauss-Lobatto
+      // nodes (Q + Q^T = B), so only the two end nodes carry 2 D_ii F(U_i).
+      // The line's sums go to its own slots of sO[l] (no other thread writes them).
+      constexpr int P = C::P;
+      const real* sD = sOp + n2 + 4 * n;  // DT[a * n + i] = D[i][a]
+      for (int task = tid; task < NE * 3 * n2; task += T) {
+        const int el2 = task / (3 * n2);
+        const int r = task - el2 * 3 * n2;
+        const int l = r / n2, line = r - l * n2;
+        const int a0 = line % n, a1 = line / n;
+        const int stride = l == 0 ? 1 : (l == 1 ? P : P * n);
+        const int base = l == 0 ? P * line : (l == 1 ? a0 + P * n * a1 : a0 + P * a1);
+        const real* f = sbuf + el2 * 15 * n3p + base;
+        real* o = sO + ((el2 * 3 + l) * NV) * n3p + base;
+        const int jo = (6 + 3 * l) * n3p;
+#pragma unroll
+        for (int ii = 0; ii < n; ++ii)
+#pragma unroll
+          for (int c = 0; c < NV; ++c) o[c * n3p + ii * stride] = real(0);
+#pragma unroll
+        for (int ii = 0; ii < n; ++ii) {
+          const real* fi = f + ii * stride;
+          const real ri = fi[0], ui = fi[n3p], vi = fi[2 * n3p], wi = fi[3 * n3p], pi = fi[4 * n3p];
+          const real Hi = fi[5 * n3p], ji0 = fi[jo], ji1 = fi[jo + n3p], ji2 = fi[jo + 2 * n3p];
+          real ai[NV];
+#pragma unroll
+          for (int c = 0; c < NV; ++c) ai[c] = real(0);
+          if (ii == 0 || ii == n - 1) {  // 2 D_ii F#(i, i) = 2 D_ii Fcal^{c,l}(U_i)
+            const real dd = real(2) * sD[ii * n + ii];
+            const real uc = ui * ji0 + vi * ji1 + wi * ji2;
+            const real m = dd * ri * uc;
+            ai[0] = m;
+            ai[1] = m * ui + dd * pi * ji0;
+            ai[2] = m * vi + dd * pi * ji1;
+            ai[3] = m * wi + dd * pi * ji2;
+            ai[4] = m * Hi;
+          }
+#pragma unroll
+          for (int aa = ii + 1; aa < n; ++aa) {
+            const real* fa = f + aa * stride;
+            // pair sums (twice the arithmetic means)
+            const real rs = ri + fa[0], us = ui + fa[n3p], vs = vi + fa[2 * n3p], ws = wi + fa[3 * n3p];
+            const real ps = pi + fa[4 * n3p], Hs = Hi + fa[5 * n3p];
+            const real j0 = ji0 + fa[jo], j1 = ji1 + fa[jo + n3p], j2 = ji2 + fa[jo + 2 * n3p];
+            const real m = real(0.125) * rs * (us * j0 + vs * j1 + ws * j2);  // {rho} {u . Ja^l}
+            const real hp = real(0.5) * ps;
+            // 2 F#: mass 2 m; momentum m u_s + (p_s / 2) Ja_s; energy m H_s
+            const real F0 = real(2) * m, F1 = m * us + hp * j0, F2 = m * vs + hp * j1, F3 = m * ws + hp * j2;
+            const real F4 = m * Hs;
+            const real dia = sD[aa * n + ii], dai = sD[ii * n + aa];
+            ai[0] += dia * F0; ai[1] += dia * F1; ai[2] += dia * F2; ai[3] += dia * F3; ai[4] += dia * F4;
+            real* oa = o + aa * stride;
+            oa[0] += dai * F0;
+            oa[n3p] += dai * F1;
+            oa[2 * n3p] += dai * F2;
+            oa[3 * n3p] += dai * F3;
+            oa[4 * n3p] += dai * F4;
+          }
+          real* oi = o + ii * stride;
+#pragma unroll
+          for (int c = 0; c < NV; ++c) oi[c * n3p] += ai[c];
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int l = 0; l < 3; ++l)
+#pragma unroll
+        for (int v = 0; v < NV; ++v) acc[v] += sO[((el * 3 + l) * NV + v) * n3p + pn];
+    }
 #pragma unroll
     for (int l = 0; l < 3; ++l) {
       const int il = l == 0 ? i : (l == 1 ? j : k);
-      const real J0 = jac[l * 3], J1 = jac[l * 3 + 1], J2 = jac[l * 3 + 2];
-      real sm[NV];
-#pragma unroll
-      for (int v = 0; v < NV; ++v) sm[v] = real(0);
-#pragma unroll
-      for (int a = 0; a < n; ++a) {
-        const int pa = l == 0 ? pidx<n>(a, j, k) : (l == 1 ? pidx<n>(i, a, k) : pidx<n>(i, j, a));
-        const real* f = myb + pa;
-        // pair sums (twice the arithmetic means)
-        const real rs = W[0] + f[0], us = W[1] + f[n3p], vs = W[2] + f[2 * n3p], ws = W[3] + f[3 * n3p];
-        const real ps = W[4] + f[4 * n3p], Hs = H + f[5 * n3p];
-        const real j0 = J0 + f[(6 + 3 * l) * n3p], j1 = J1 + f[(7 + 3 * l) * n3p], j2 = J2 + f[(8 + 3 * l) * n3p];
-        const real m = real(0.125) * rs * (us * j0 + vs * j1 + ws * j2);  // {rho} {u . Ja^l}
-        const real d = sD[a * n + il];
-        const real dm = d * m, dp = real(0.5) * d * ps;
-        // 2 D F#: mass 2 dm; momentum dm u_s + (d p_s / 2) Ja_s; energy dm H_s
-        sm[0] += dm;
-        sm[1] += dm * us + dp * j0;
-        sm[2] += dm * vs + dp * j1;
-        sm[3] += dm * ws + dp * j2;
-        sm[4] += dm * Hs;
-      }
-      acc[0] += real(2) * sm[0];
-#pragma unroll
-      for (int v = 1; v < NV; ++v) acc[v] += sm[v];
       // face terms of the strong form: -(+-1) l_hat(+-1) Fcal^{c,l} at the line's end nodes
       if (il == 0 || il == n - 1) {
+        const real J0 = jac[l * 3], J1 = jac[l * 3 + 1], J2 = jac[l * 3 + 2];
         const real c = il == 0 ? sOp[n2 + 2 * n] : -sOp[n2 + 3 * n + n - 1];
         const real uc = W[1] * J0 + W[2] * J1 + W[3] * J2;
         const real mf = Uo[1] * J0 + Uo[2] * J1 + Uo[3] * J2;
@@ -576,7 +655,8 @@ constexpr size_t lift_vol_smem() {
   using C = Cfg<n>;
   // the FP64 form sweeps per node and needs no result buffer
   constexpr int out = (sizeof(real) == 8 && SW == 0) ? 0 : C::NE * NV * C::n3p;
-  return sizeof(real) * (C::NE * 15 * C::n3p + out + C::NE * 6 * 15 * C::n2 + C::n2 + 4 * n + (SPLIT ? C::n2 : 0)) +
+  return sizeof(real) * (C::NE * 15 * C::n3p + out + C::NE * 6 * 15 * C::n2 + C::n2 + 4 * n +
+                         (SPLIT ? C::n2 : 0) + ((SPLIT && sizeof(real) == 8) ? C::NE * 3 * NV * C::n3p : 0)) +
          sizeof(int) * C::NE * 6;
 }
 
