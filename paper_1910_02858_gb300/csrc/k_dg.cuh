@@ -47,7 +47,7 @@ __device__ __forceinline__ void line_sweep3(const real* __restrict__ buf, real* 
   using C = Cfg<n>;
   constexpr int n2 = C::n2, n3p = C::n3p, P = C::P, NE = C::NE, T = C::T;
   constexpr int L = NE * NV * n2;
-#pragma unroll 1
+#pragma unroll
   for (int l = 0; l < 3; ++l) {
     const int stride = l == 0 ? 1 : (l == 1 ? P : P * n);
     for (int it = tid; it < L; it += T) {
@@ -409,11 +409,11 @@ __global__ void __launch_bounds__(Cfg<n>::T) k_lift_vol(
     // one pass per line of direction l gives the values on both faces -l and +l;
     // the face node of the line has (p, q) = its free indices
     constexpr int P = C::P;
-    for (int it = tid; it < NE * 3 * 15 * n2; it += T) {
-      const int el2 = it / (3 * 15 * n2);
-      int r = it - el2 * 3 * 15 * n2;
-      const int l = r / (15 * n2);
-      r -= l * 15 * n2;
+#pragma unroll
+    for (int l = 0; l < 3; ++l)
+    for (int it = tid; it < NE * 15 * n2; it += T) {
+      const int el2 = it / (15 * n2);
+      const int r = it - el2 * 15 * n2;
       const int c = r / n2, line = r - c * n2;
       if (e0 + el2 >= K) continue;
       const int p = line % n, q = line / n;
