@@ -14,6 +14,8 @@
 // threads for small n.  Line sweeps of D_hat read the element's staged fields
 // from shared memory; the per-node results stay in registers.
 #pragma once
+#include <type_traits>
+
 #include "dg_common.cuh"
 #include "k_tc.cuh"
 #include "launch.h"
@@ -147,13 +149,12 @@ __device__ __forceinline__ void faces_from_volume(const real* __restrict__ sU, c
     }
     return;
   }
-  for (int it = tid; it < C::NE * 3 * n2; it += C::T) {
-    const int el = it / (3 * n2);
-    const int r = it - el * 3 * n2;
-    const int l = r / n2, line = r - l * n2;
-    if (e0 + el >= K) continue;
+  // items are grouped by direction in runs of n^2 (whole warps for n >= 6): the
+  // switch gives each direction compile-time line strides
+  auto line_item = [&](auto Lc, int el, int line) {
+    constexpr int l = decltype(Lc)::value;
     const int p = line % n, q = line / n;
-    const int stride = l == 0 ? 1 : (l == 1 ? P : P * n);
+    constexpr int stride = l == 0 ? 1 : (l == 1 ? P : P * n);
     const int base = l == 0 ? P * line : (l == 1 ? p + P * n * q : p + P * q);
     real Um[NV], Up[NV];
 #pragma unroll
@@ -177,8 +178,10 @@ __device__ __forceinline__ void faces_from_volume(const real* __restrict__ sU, c
     }
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      real W[NV];
-      cons_to_prim(h ? Up : Um, W, ph);
+      real W[NV], Uh[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) Uh[v] = h ? Up[v] : Um[v];
+      cons_to_prim(Uh, W, ph);
       if (!(W[0] > real(0)) || !(W[4] > real(0))) atomicOr(status, 1u);
       const int es = sES[el * 6 + 2 * l + h];
       const int mpq = orient_pq(es_orient(es), n - 1, p, q);
@@ -186,6 +189,18 @@ __device__ __forceinline__ void faces_from_volume(const real* __restrict__ sU, c
 #pragma unroll
       for (int v = 0; v < NV; ++v) dst[v * n2] = W[v];
     }
+  };
+  for (int it = tid; it < C::NE * 3 * n2; it += C::T) {
+    const int el = it / (3 * n2);
+    const int r = it - el * 3 * n2;
+    const int l = r / n2, line = r - l * n2;
+    if (e0 + el >= K) continue;
+    if (l == 0)
+      line_item(std::integral_constant<int, 0>{}, el, line);
+    else if (l == 1)
+      line_item(std::integral_constant<int, 1>{}, el, line);
+    else
+      line_item(std::integral_constant<int, 2>{}, el, line);
   }
 }
 
