@@ -102,7 +102,7 @@ __device__ __forceinline__ void tc_sweep3(const float* __restrict__ buf, float* 
   const int warp = tid >> 5, lane = tid & 31;
   const int nwarps = T >> 5;  // only full warps issue mma
   const int gid = lane >> 2, tig = lane & 3;
-#pragma unroll 1
+#pragma unroll
   for (int l = 0; l < 3; ++l) {
     if (warp < nwarps) {
       for (int tile = warp; tile < tiles; tile += nwarps) {
