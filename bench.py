@@ -556,7 +556,42 @@ def adjoint_ratio(dev, F, wl, Solver, SolverConfig, torch):
         res[label] = {"forward_ms": times["forward"] * 1e3, "gradient_ms": times["gradient"] * 1e3,
                       "ratio": times["gradient"] / times["forward"]}
         s.close()
+    res["c5_fp32_vs_fp64"] = adjoint_fp32_error(dev, F, wl, Solver, SolverConfig, torch, final_state)
     return res
+
+
+def adjoint_fp32_error(dev, F, wl, Solver, SolverConfig, torch, final_state):
+    """C5 forward and gradient in the FP32 form against FP64: relative L2 of the
+    final state (momentum against the momentum-vector norm), of J and of dJ/dU0."""
+    import math
+
+    import numpy as np
+
+    N, nsteps, dt = 5, 40, 1e-3
+    mesh = wl.box_mesh((8, 8, 8), Ngeo=1)
+    U0 = wl.taylor_green(mesh.node_coords(N, 0))
+    # J = sum_nodes w_i w_j w_k J_e |m|^2 / (2 rho): Gauss weights (numpy), affine elements of width 2 pi / 8
+    w = np.polynomial.legendre.leggauss(N + 1)[1]
+    w3 = np.einsum("k,j,i->kji", w, w, w) * (math.pi / 8) ** 3
+    out = {}
+    for name, prec, dtype in (("fp64", F.FP64, torch.float64), ("fp32", F.FP32, torch.float32)):
+        s = Solver(SolverConfig(N=N, riemann=F.RIEMANN_ROE_SMOOTH, mu=1 / 400.0, precision=prec), mesh.coords,
+                   mesh.conn, device=dev)
+        try:
+            wJ = torch.tensor(w3, device=dev, dtype=dtype)
+            U0d = torch.tensor(U0, device=dev, dtype=dtype, requires_grad=True)
+            UT = final_state(U0d, s, nsteps, dt, 0.0, 20)
+            J = (wJ * 0.5 * (UT[:, 1] ** 2 + UT[:, 2] ** 2 + UT[:, 3] ** 2) / UT[:, 0]).sum()
+            J.backward()
+            out[name] = (UT.detach().double(), U0d.grad.detach().double(), float(J))
+        finally:
+            s.close()
+    (U64, g64, J64), (U32, g32, J32) = out["fp64"], out["fp32"]
+    d = (U32 - U64).transpose(0, 1).reshape(5, -1).norm(dim=1)
+    r = U64.transpose(0, 1).reshape(5, -1).norm(dim=1)
+    r[1:4] = U64[:, 1:4].norm()
+    return {"state_rel_l2": (d / r).tolist(), "J_rel": abs(J32 - J64) / abs(J64),
+            "grad_rel_l2": float((g32 - g64).norm() / g64.norm())}
 
 
 if __name__ == "__main__":

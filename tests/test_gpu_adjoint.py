@@ -146,3 +146,32 @@ def test_c5_gradient_vs_oracle_adjoint(c5):
     Jo, go = dg.gradient_ke(torch.tensor(U0), nsteps, dt)
     assert abs(Jo - float(J)) < 1e-12 * abs(Jo)
     assert float((U0d.grad.cpu() - go).norm() / go.norm()) < 1e-10
+
+
+def _c5_run(s, mesh, sk, U0, dtype):
+    from paper_1910_02858_gb300.adjoint import final_state
+
+    wJ = torch.tensor(_oracle(sk, mesh).quad_weights().numpy(), device=DEV, dtype=dtype)
+    U0d = torch.tensor(U0, device=DEV, dtype=dtype, requires_grad=True)
+    UT = final_state(U0d, s, 40, 1e-3, 0.0, 20)
+    J = (wJ * 0.5 * (UT[:, 1] ** 2 + UT[:, 2] ** 2 + UT[:, 3] ** 2) / UT[:, 0]).sum()
+    J.backward()
+    return UT.detach().double().cpu(), U0d.grad.detach().double().cpu(), float(J)
+
+
+def test_c5_fp32_forward_and_adjoint_error(c5):
+    """C5 in the FP32 form (forward and discrete adjoint in FP32 arithmetic)
+    against the FP64 path: the final state (momentum components against the norm
+    of the momentum vector), the functional and the gradient dJ/dU0 stay within
+    the 1e-5 relative L2 budget of the precision form."""
+    mesh, s64, sk, U0 = c5
+    s32 = _solver(dict(sk, precision=1), mesh)
+    U64, g64, J64 = _c5_run(s64, mesh, sk, U0, torch.float64)
+    U32, g32, J32 = _c5_run(s32, mesh, sk, U0, torch.float32)
+    s32.close()
+    d = (U32 - U64).transpose(0, 1).reshape(5, -1).norm(dim=1)
+    r = U64.transpose(0, 1).reshape(5, -1).norm(dim=1)
+    r[1:4] = U64[:, 1:4].norm()
+    assert float((d / r).max()) < 1e-5, (d / r).tolist()
+    assert abs(J32 - J64) < 1e-5 * abs(J64)
+    assert float((g32 - g64).norm() / g64.norm()) < 1e-5
