@@ -66,6 +66,8 @@ def kernel_source_hash() -> str:
 # GB300 FP64 FMA peak derived from unit counts and clocks: 152 SMs x 2 DFMA/clk
 # (4 FP64 flop/clk/SM, consistent with the nominal 1.25 TFLOP/s) x 2070 MHz.
 FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12
+# FP32 FMA peak from the same unit counts: 128 FP32 lanes x 2 flop/clk per SM
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 
 
 class ClockSampler:
@@ -335,6 +337,16 @@ def main():
                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks() else "fallback 6.8 TB/s",
                     "kernel_share": share}
     step_bytes_gbs = bytes_stage * dof * NSTAGES / (ms_step * 1e-3) / 1e9
+    # whole-step roofline: the slower of the step's algorithmic bytes over the measured HBM
+    # bandwidth and its algorithmic flops at the form's FMA peak (the library's own counts)
+    bps = s.query(F.Q_BYTES_PER_STAGE) / dof
+    fps = s.query(F.Q_FLOPS_PER_STAGE) / dof
+    fpk = FP64_PEAK_TFLOPS if args.form == "fp64" else FP32_PEAK_TFLOPS
+    t_mem, t_alu = bps / peaks().get("hbm_gbs", 6800.0), fps / (fpk * 1e3)  # ns per DOF and stage
+    step_roofline = {"bound": "alu" if t_alu > t_mem else "hbm", "floor_ns": max(t_mem, t_alu),
+                     "achieved_ns": pid * world, "frac": max(t_mem, t_alu) / (pid * world),
+                     "bytes_per_dof": bps, "flops_per_dof": fps, "alu_peak_tflops": fpk,
+                     "alu_peak_source": "derived from unit counts at 2070 MHz"}
     kernels = {k: {"ms_per_launch": (v[0] / v[1]) if v[1] else 0.0, "launches": v[1]} for k, v in ktimes.items() if v[1]}
 
     # end to end through the public API with host buffers (H2D + step + D2H per step)
@@ -357,7 +369,7 @@ def main():
             "clocks": clk.summary(), "gpu_launches": launches_per_step * args.steps,
             "e2e": {"value": e2e_pid, "unit": UNIT, "h2d_bytes_per_step": ubytes, "d2h_bytes_per_step": ubytes},
             "roofline": roofline, "dof_updates_per_s": dof * world / (pid * 1e-9 * dof * world) if pid else None,
-            "step_algorithmic_hbm_gbs": step_bytes_gbs, "kernels": kernels}
+            "step_algorithmic_hbm_gbs": step_bytes_gbs, "step_roofline": step_roofline, "kernels": kernels}
 
     if rank == 0 and not args.no_extras:
         line["extras"] = extras(args, s, U0, mesh, dt, dev, F, wl, Solver, SolverConfig, torch, np)
@@ -421,7 +433,10 @@ def extras(args, s64, U0, mesh, dt, dev, F, wl, Solver, SolverConfig, torch, np)
             n = 8
             bytes_stage = (46.0 + 117.0 * 3.0 / n) * 4 * dof
             lv = kt["lift_vol"][0] / max(kt["lift_vol"][1], 1)
-            out[name] = {"pid": ms * 1e6 / (nsteps * NSTAGES * dof), "steps": nsteps,
+            pid32 = ms * 1e6 / (nsteps * NSTAGES * dof)
+            floor = max(s.query(F.Q_BYTES_PER_STAGE) / dof / peaks().get("hbm_gbs", 6800.0),
+                        s.query(F.Q_FLOPS_PER_STAGE) / dof / (FP32_PEAK_TFLOPS * 1e3))
+            out[name] = {"pid": pid32, "step_roofline_frac": floor / pid32, "steps": nsteps,
                          "rel_l2_err_vs_fp64": rel_err_per_var(U, U64),
                          "step_algorithmic_hbm_gbs": bytes_stage * NSTAGES * nsteps / (ms * 1e-3) / 1e9,
                          "lift_vol_ms_per_launch": lv,

@@ -802,8 +802,10 @@ flexi_status flexi_query(flexi_ctx* c, int what, int64_t* val) {
       return FLEXI_OK;
     }
     case FLEXI_Q_FLOPS_PER_STAGE: {
-      // per DOF: D_hat sweeps 2*(45+15) n; LG prolongation of U and grad U and the
-      // two surface integrals 2*(4*6*20)/... see DESIGN; pointwise ~100; faces 300 f; RK 4
+      // per DOF, FMA = 2: D_hat sweeps 2 (45 + 15) n; Gauss nodes: prolongation of U (5)
+      // and of the gradients (15) to 6 faces and the two surface integrals, each 2 * 6 * 20
+      // (Gauss-Lobatto: surface terms at face nodes only); contravariant transforms 2 * 90;
+      // pointwise fluxes ~100; face fluxes ~300 per face node (f per DOF); RK update 4
       const bool lg = c->p.node_type == FLEXI_NODES_GAUSS;
       const double sweeps = 2.0 * 60.0 * n;
       const double surf = lg ? 2.0 * (6 * 5 + 6 * 15 + 6 * 5 + 6 * 15) : 2.0 * (6 * 5 + 6 * 15) * (1.0 / n) * 2;
