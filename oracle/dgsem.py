@@ -58,6 +58,11 @@ RK_C = [0.0,
         2802321613138.0 / 2924317926251.0]
 
 ROE, HLLC, RUSANOV = 0, 1, 3
+# boundary conditions (Sec. 2.2 names Dirichlet, inflow/outflow and wall conditions, imposed
+# weakly through the outer state of the numerical flux): the outer state U_R is the exact
+# solution, the inner state (outflow: extrapolation), or the inner state with its normal
+# velocity reversed (slip wall); every kind takes the inner lifted gradients, g_R = g_L
+BC_EXACT, BC_OUTFLOW, BC_SLIP_WALL = 0, 1, 2
 
 
 @dataclass
@@ -73,6 +78,7 @@ class Params:
     bc_exact: object = eq.EXACT_TGV  # exact function id (or callable (x, t) -> U) on Dirichlet sides
     source: bool = False  # manufactured-solution source term
     split: str = ""  # "" standard weak form; "pirozzoli" / "central": split form (LGL only)
+    bc_kinds: dict = None  # boundary id -> BC_EXACT (default), BC_OUTFLOW, BC_SLIP_WALL
 
 
 class DGSEM:
@@ -114,6 +120,14 @@ class DGSEM:
                 Ub = self.p.bc_exact(xb, t)
             else:
                 Ub = eq.exact_state(self.p.bc_exact, xb, t, gas, self.p.Ma)
+            kinds = self.p.bc_kinds or {}
+            kind = torch.tensor([kinds.get(int(geo.bc[sd]), BC_EXACT) for sd in bnd.tolist()])
+            Ui = UL[bnd].movedim(1, -1)  # [B,q,p,5] inner state
+            nb = geo.nvec[bnd].movedim(1, -1)  # [B,q,p,3] outward normal of the element
+            mn = (Ui[..., 1:4] * nb).sum(-1, keepdim=True)
+            Umirror = torch.cat([Ui[..., :1], Ui[..., 1:4] - 2.0 * mn * nb, Ui[..., 4:]], dim=-1)
+            k = kind.view(-1, 1, 1, 1)
+            Ub = torch.where(k == BC_OUTFLOW, Ui, torch.where(k == BC_SLIP_WALL, Umirror, Ub))
             UR = UR.clone(); WR = WR.clone()
             UR[bnd] = Ub.movedim(-1, 1)
             WR[bnd] = eq.prim(Ub, gas).movedim(-1, 1)
