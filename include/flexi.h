@@ -68,6 +68,12 @@ enum { FLEXI_FP64 = 0, FLEXI_FP32 = 1, FLEXI_FP32_TF32 = 2, FLEXI_FP32_BF16 = 3 
  * flux of the paper's NACA 64418 computation, Sec. 7.1) and metric terms averaged
  * over each pair; viscous fluxes stay in the standard form. */
 enum { FLEXI_SPLIT_STANDARD = 0, FLEXI_SPLIT_KEP = 1 };
+/* Boundary kinds (Sec. 2.2: boundary conditions enter weakly through the outer
+ * state of the numerical flux; the inner lifted gradients are used outside):
+ * EXACT: the exact state FLEXI_EXACT_* at the face nodes (Dirichlet; the default);
+ * OUTFLOW: the inner state (extrapolation, supersonic outflow);
+ * SLIP_WALL: the inner state with its normal velocity reversed (inviscid wall). */
+enum { FLEXI_BC_EXACT = 0, FLEXI_BC_OUTFLOW = 1, FLEXI_BC_SLIP_WALL = 2 };
 /* Exact states for Dirichlet sides (and the manufactured source term). */
 enum { FLEXI_EXACT_TGV = 0, FLEXI_EXACT_FREESTREAM = 1, FLEXI_EXACT_MANUFACTURED = 2 };
 
@@ -122,6 +128,11 @@ flexi_status flexi_mesh_init(flexi_ctx **out, const flexi_params *p, int K, cons
 #define FLEXI_CONN_MORTAR (-1073741824)
 flexi_status flexi_mesh_init_mortar(flexi_ctx **out, const flexi_params *p, int K, const double *coords,
                                     const int32_t *conn, int M, const int32_t *mortars, void *stream);
+
+/* Boundary kind of every side with boundary id bc_id (conn value -1 - bc_id).
+ * Returns FLEXI_EINVAL for an unknown kind or an id no boundary side carries.
+ * Synchronous (copies a small table to the device); call it between time steps. */
+flexi_status flexi_set_bc(flexi_ctx *ctx, int bc_id, int kind);
 
 /* Ut = L(U, t): the semi-discrete right-hand side, Eq. semiDiscrete with the
  * BR1 gradients of Eq. discreteGradient (steps: prolongation, lifting, face

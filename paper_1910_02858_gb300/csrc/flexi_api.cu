@@ -41,6 +41,9 @@ struct flexi_ctx {
   double *Ja64 = nullptr, *sJ64 = nullptr, *wJ = nullptr, *xsol = nullptr, *fgeo64 = nullptr, *xbc = nullptr;
   float *Ja32 = nullptr, *sJ32 = nullptr, *fgeo32 = nullptr;
   int* elemSide = nullptr;
+  int* bcKind = nullptr;       // device [nBC]
+  std::vector<int> bcId;       // host: boundary id of every boundary side
+  std::vector<int> bcKindHost;
   unsigned* status = nullptr;
   double* partial = nullptr;
   double* partial_host = nullptr;
@@ -326,6 +329,9 @@ flexi_status mesh_init_impl(flexi_ctx* c, const flexi_params* p, int K, const do
   if (nMarked != nMortarSides) return FLEXI_EMESH;
   const int nV = nMortarSides - M;
   c->nBC = (int)bnd_pairs.size();
+  c->bcId.clear();
+  for (int key : bnd_pairs) c->bcId.push_back(-1 - conn[key * 3]);
+  c->bcKindHost.assign(c->nBC, FLEXI_BC_EXACT);
   c->nMortar = M;
   c->S = c->nBC + (int)inner_pairs.size() + nV + M;
   sideMaster.resize(2 * c->S);
@@ -412,6 +418,7 @@ flexi_status mesh_init_impl(flexi_ctx* c, const flexi_params* p, int K, const do
   AL(c->wJ, (size_t)K * n3);
   AL(c->fgeo64, (size_t)S * 4 * n2);
   AL(c->xbc, (size_t)std::max(c->nBC, 1) * 3 * n2);
+  AL(c->bcKind, (size_t)std::max(c->nBC, 1));  // zero: every boundary takes the exact state
   AL(c->elemSide, (size_t)K * 6);
   AL(c->status, 1);
   if (p->source) AL(c->xsol, (size_t)K * 3 * n3);
@@ -530,6 +537,7 @@ flexi_status mesh_init_impl(flexi_ctx* c, const flexi_params* p, int K, const do
   }
   c->m.elemSide = c->elemSide;
   c->m.xbc = c->xbc;
+  c->m.bcKind = c->bcKind;
   c->m.xsol = c->xsol;
   c->m.status = c->status;
   c->m.sweep_mode = p->precision == FLEXI_FP32_TF32 ? 1 : (p->precision == FLEXI_FP32_BF16 ? 2 : 0);
@@ -707,6 +715,19 @@ flexi_status flexi_mesh_init_mortar(flexi_ctx** out, const flexi_params* p, int 
     return s;
   }
   *out = c;
+  return FLEXI_OK;
+}
+
+flexi_status flexi_set_bc(flexi_ctx* c, int bc_id, int kind) {
+  if (c == nullptr || kind < FLEXI_BC_EXACT || kind > FLEXI_BC_SLIP_WALL) return FLEXI_EINVAL;
+  bool found = false;
+  for (int b = 0; b < c->nBC; ++b)
+    if (c->bcId[b] == bc_id) {
+      c->bcKindHost[b] = kind;
+      found = true;
+    }
+  if (!found) return FLEXI_EINVAL;
+  CK(cudaMemcpy(c->bcKind, c->bcKindHost.data(), sizeof(int) * c->nBC, cudaMemcpyHostToDevice));
   return FLEXI_OK;
 }
 

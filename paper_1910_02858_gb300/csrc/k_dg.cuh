@@ -228,21 +228,39 @@ __global__ void __launch_bounds__(Cfg<n>::T) k_prolong(const real* __restrict__ 
 }
 
 // ---------------------------------------------------------------------------
-// Dirichlet boundary sides: outer state = exact state at the face nodes
+// boundary sides (weakly imposed through the outer state of the flux): exact state
+// at the face nodes (kind 0), the inner state (1, outflow), or the inner state with
+// its normal velocity reversed (2, slip wall; the normal is the element's outward one)
 // ---------------------------------------------------------------------------
 template <typename real, int n>
-__global__ void k_bc(const double* __restrict__ xbc, real* __restrict__ Wf, int S, int nBC, double t,
-                     Phys<real> ph) {
+__global__ void k_bc(const double* __restrict__ xbc, const int* __restrict__ bcKind, const real* __restrict__ fgeo,
+                     real* __restrict__ Wf, int S, int nBC, double t, Phys<real> ph) {
   constexpr int n2 = n * n;
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= nBC * n2) return;
   const int b = idx / n2, pq = idx - b * n2;
-  double x[3];
+  const int kind = bcKind[b];
+  real W[NV];
+  if (kind == 0) {
+    double x[3];
 #pragma unroll
-  for (int c = 0; c < 3; ++c) x[c] = xbc[((size_t)b * 3 + c) * n2 + pq];
-  real U[NV], W[NV];
-  exact_state<real>(ph.bc_exact, x, t, ph, U);
-  cons_to_prim(U, W, ph);
+    for (int c = 0; c < 3; ++c) x[c] = xbc[((size_t)b * 3 + c) * n2 + pq];
+    real U[NV];
+    exact_state<real>(ph.bc_exact, x, t, ph, U);
+    cons_to_prim(U, W, ph);
+  } else {
+    const real* src = Wf + ((size_t)b * NV) * n2 + pq;  // slot 0: the element's face state
+#pragma unroll
+    for (int v = 0; v < NV; ++v) W[v] = src[v * n2];
+    if (kind == 2) {
+      const real* g = fgeo + ((size_t)b * 4) * n2 + pq;
+      const real nx = g[0], ny = g[n2], nz = g[2 * n2];
+      const real un = W[1] * nx + W[2] * ny + W[3] * nz;
+      W[1] -= real(2) * un * nx;
+      W[2] -= real(2) * un * ny;
+      W[3] -= real(2) * un * nz;
+    }
+  }
   real* dst = Wf + ((size_t)(S + b) * NV) * n2 + pq;
 #pragma unroll
   for (int v = 0; v < NV; ++v) dst[v * n2] = W[v];
@@ -846,7 +864,8 @@ template <typename real>
 cudaError_t launch_bc(const DevMesh& m, double t, const Phys<real>& ph, cudaStream_t st) {
   if (m.nBC == 0) return cudaSuccess;
   const int tot = m.nBC * m.n * m.n;
-  FLEXI_DISPATCH_N(m.n, (k_bc<real, NN><<<(tot + 127) / 128, 128, 0, st>>>(m.xbc, (real*)m.Wf, m.S, m.nBC, t, ph)));
+  FLEXI_DISPATCH_N(m.n, (k_bc<real, NN><<<(tot + 127) / 128, 128, 0, st>>>(m.xbc, m.bcKind, (const real*)m.fgeo,
+                                                                          (real*)m.Wf, m.S, m.nBC, t, ph)));
   return cudaGetLastError();
 }
 

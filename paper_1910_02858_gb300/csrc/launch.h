@@ -19,6 +19,7 @@ struct DevMesh {
   const void* fgeo = nullptr;  // [S][4][n^2]   n_hat (3), s_hat
   const int* elemSide = nullptr;  // [K][6] packed (side<<4 | slave<<3 | orient)
   const double* xbc = nullptr;    // [nBC][3][n^2] face node coordinates of boundary sides
+  const int* bcKind = nullptr;    // [nBC] 0 exact state, 1 outflow, 2 slip wall
   const double* xsol = nullptr;   // [K][3][n^3] (only with a source term)
   void* Wf = nullptr;          // [2][S][5][n^2] primitive face states (slot 0 master, 1 slave/boundary)
   void* Gf = nullptr;          // [2][S][15][n^2] lifted gradients on the faces (index d*5+v)

@@ -21,11 +21,12 @@ FP64, FP32, FP32_TF32, FP32_BF16 = 0, 1, 2, 3
 EXACT_TGV, EXACT_FREESTREAM, EXACT_MANUFACTURED = 0, 1, 2
 SPLIT_STANDARD, SPLIT_KEP = 0, 1
 CONN_MORTAR = -(1 << 30)
+BC_EXACT, BC_OUTFLOW, BC_SLIP_WALL = 0, 1, 2
 Q_K, Q_N, Q_NSIDES, Q_NBCSIDES, Q_DOF, Q_BYTES_PER_STAGE, Q_FLOPS_PER_STAGE, Q_STATUS, Q_DEVICE_BYTES, Q_PRECISION = range(10)
 KERNEL_CLASSES = ["lift_vol", "face", "surf_rk", "prolong", "bc", "adjoint", "reduce", "other"]
 
 # every entry point declared in include/flexi.h
-EXPORTS = ["flexi_mesh_init", "flexi_mesh_init_mortar", "flexi_rhs", "flexi_rk_step", "flexi_rk_step_stages", "flexi_adjoint_step",
+EXPORTS = ["flexi_mesh_init", "flexi_mesh_init_mortar", "flexi_set_bc", "flexi_rhs", "flexi_rk_step", "flexi_rk_step_stages", "flexi_adjoint_step",
            "flexi_rhs_adjoint", "flexi_rk_run_host", "flexi_reduce", "flexi_reduce_noalloc", "flexi_query",
            "flexi_profile", "flexi_kernel_times", "flexi_strerror", "flexi_destroy"]
 NOALLOC_MAX_ELEMENTS = 65536
@@ -58,6 +59,7 @@ def lib() -> ctypes.CDLL:
         vp, d, i, i64p = ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)
         L.flexi_mesh_init.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(flexi_params), i, vp, vp, vp]
         L.flexi_mesh_init_mortar.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(flexi_params), i, vp, vp, i, vp, vp]
+        L.flexi_set_bc.argtypes = [vp, i, i]
         L.flexi_rhs.argtypes = [vp, vp, vp, d, vp]
         L.flexi_rk_step.argtypes = [vp, vp, vp, d, d, vp]
         L.flexi_rk_step_stages.argtypes = [vp, vp, vp, d, d, vp, vp]
@@ -119,6 +121,10 @@ def flexi_mesh_init_mortar(params: flexi_params, coords: np.ndarray, conn: np.nd
                                        int(mortars.shape[0]), mortars.ctypes.data_as(ctypes.c_void_p),
                                        _stream(stream)), "flexi_mesh_init_mortar")
     return ctx
+
+
+def flexi_set_bc(ctx, bc_id: int, kind: int):
+    return check(lib().flexi_set_bc(ctx, int(bc_id), int(kind)), "flexi_set_bc")
 
 
 def flexi_rhs(ctx, U, Ut, t, stream=None):

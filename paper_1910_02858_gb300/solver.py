@@ -99,6 +99,10 @@ class Solver:
         out["status"] = code
         return out
 
+    def set_bc(self, bc_id: int, kind: int):
+        """Boundary kind (flexi.BC_*) of the sides with boundary id bc_id."""
+        F.flexi_set_bc(self.ctx, bc_id, kind)
+
     def query(self, what):
         return F.flexi_query(self.ctx, what)
 
