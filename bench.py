@@ -461,6 +461,10 @@ def extras(args, s64, U0, mesh, dt, dev, F, wl, Solver, SolverConfig, torch, np)
     except Exception as exc:
         out["lobatto"] = {"error": repr(exc)}
     try:
+        out["small_cases"] = small_cases_pid(dev, F, wl, Solver, SolverConfig, torch)
+    except Exception as exc:
+        out["small_cases"] = {"error": repr(exc)}
+    try:
         out["mortar"] = mortar_pid(dt, dev, F, wl, Solver, SolverConfig, torch)
     except Exception as exc:
         out["mortar"] = {"error": repr(exc)}
@@ -502,6 +506,34 @@ def lobatto_pid(mesh, dt, dev, F, wl, Solver, SolverConfig, torch):
             F.flexi_profile(s.ctx, False)
             res[name] = {"pid": ms * 1e6 / (10 * NSTAGES * s.query(F.Q_DOF)), "steps": 10,
                          "lift_vol_ms_per_launch": kt["lift_vol"][0] / max(kt["lift_vol"][1], 1)}
+        finally:
+            s.close()
+    return res
+
+
+def small_cases_pid(dev, F, wl, Solver, SolverConfig, torch):
+    """Launch-bound sizes: C1 (4^3, N = 3 LGL, Roe, dt = 1e-3) and the adjoint
+    workload's forward (8^3, N = 5, smoothed Roe): PID with every step launched
+    (flexi_rk_step) and with the CUDA-graph replay of flexi_rk_run."""
+    res = {}
+    for label, nel, N, nt, riem in (("c1_4^3_N3_lgl", 4, 3, 1, F.RIEMANN_ROE), ("c5_8^3_N5", 8, 5, 0,
+                                                                               F.RIEMANN_ROE_SMOOTH)):
+        mesh = wl.box_mesh((nel,) * 3, Ngeo=1)
+        s = Solver(SolverConfig(N=N, node_type=nt, riemann=riem), mesh.coords, mesh.conn, device=dev)
+        try:
+            U = torch.tensor(wl.taylor_green(mesh.node_coords(N, nt)), device=dev)
+            dof = s.query(F.Q_DOF)
+            out = {}
+            for mode, graph in (("launches", False), ("graph", True)):
+                s.run(U, 20, 1e-4, graph=graph)
+                torch.cuda.synchronize(dev)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                s.run(U, 200, 1e-4, graph=graph)
+                e1.record()
+                torch.cuda.synchronize(dev)
+                out[mode] = e0.elapsed_time(e1) * 1e6 / (200 * NSTAGES * dof)
+            res[label] = {"dof": dof, "pid_launches": out["launches"], "pid_graph": out["graph"]}
         finally:
             s.close()
     return res

@@ -144,6 +144,15 @@ flexi_status flexi_rhs(flexi_ctx *ctx, const void *U, void *Ut, double t, void *
  * U, dU: device, updated in place (dU is multiplied by A_1 = 0 first). */
 flexi_status flexi_rk_step(flexi_ctx *ctx, void *U, void *dU, double t, double dt, void *stream);
 
+/* nsteps calls of flexi_rk_step (times t0 + s dt), enqueued on `stream`.  When one
+ * step does not depend on t (no source term, no exact-state boundary with the
+ * time-dependent manufactured state), stream is not the legacy NULL stream and
+ * kernel timing is off, the first step runs eagerly and the rest replay a CUDA
+ * graph of one step, captured once per (U, dU, dt, stream) and kept in the
+ * context (same kernels in the same order, so the results are identical).
+ * U, dU: device, updated in place. */
+flexi_status flexi_rk_run(flexi_ctx *ctx, void *U, void *dU, int nsteps, double t0, double dt, void *stream);
+
 /* As flexi_rk_step, and also stores the five stage inputs U_{k-1} into
  * U_stages (device, [5][K][5][n^3]) for the adjoint. */
 flexi_status flexi_rk_step_stages(flexi_ctx *ctx, void *U, void *dU, double t, double dt, void *U_stages,

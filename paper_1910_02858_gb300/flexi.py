@@ -26,7 +26,7 @@ Q_K, Q_N, Q_NSIDES, Q_NBCSIDES, Q_DOF, Q_BYTES_PER_STAGE, Q_FLOPS_PER_STAGE, Q_S
 KERNEL_CLASSES = ["lift_vol", "face", "surf_rk", "prolong", "bc", "adjoint", "reduce", "other"]
 
 # every entry point declared in include/flexi.h
-EXPORTS = ["flexi_mesh_init", "flexi_mesh_init_mortar", "flexi_set_bc", "flexi_rhs", "flexi_rk_step", "flexi_rk_step_stages", "flexi_adjoint_step",
+EXPORTS = ["flexi_mesh_init", "flexi_mesh_init_mortar", "flexi_set_bc", "flexi_rhs", "flexi_rk_step", "flexi_rk_run", "flexi_rk_step_stages", "flexi_adjoint_step",
            "flexi_rhs_adjoint", "flexi_rk_run_host", "flexi_reduce", "flexi_reduce_noalloc", "flexi_query",
            "flexi_profile", "flexi_kernel_times", "flexi_strerror", "flexi_destroy"]
 NOALLOC_MAX_ELEMENTS = 65536
@@ -62,6 +62,7 @@ def lib() -> ctypes.CDLL:
         L.flexi_set_bc.argtypes = [vp, i, i]
         L.flexi_rhs.argtypes = [vp, vp, vp, d, vp]
         L.flexi_rk_step.argtypes = [vp, vp, vp, d, d, vp]
+        L.flexi_rk_run.argtypes = [vp, vp, vp, i, d, d, vp]
         L.flexi_rk_step_stages.argtypes = [vp, vp, vp, d, d, vp, vp]
         L.flexi_adjoint_step.argtypes = [vp, vp, vp, vp, d, d, vp]
         L.flexi_rhs_adjoint.argtypes = [vp, vp, vp, vp, d, vp]
@@ -133,6 +134,11 @@ def flexi_rhs(ctx, U, Ut, t, stream=None):
 
 def flexi_rk_step(ctx, U, dU, t, dt, stream=None):
     return check(lib().flexi_rk_step(ctx, _ptr(U), _ptr(dU), float(t), float(dt), _stream(stream)), "flexi_rk_step")
+
+
+def flexi_rk_run(ctx, U, dU, nsteps, t0, dt, stream=None):
+    return check(lib().flexi_rk_run(ctx, _ptr(U), _ptr(dU), int(nsteps), float(t0), float(dt), _stream(stream)),
+                 "flexi_rk_run")
 
 
 def flexi_rk_step_stages(ctx, U, dU, t, dt, U_stages, stream=None):

@@ -75,11 +75,20 @@ class Solver:
         self._check(U, dU)
         F.flexi_rk_step_stages(self.ctx, U, dU, t, dt, stages, self._stream())
 
-    def run(self, U, nsteps, dt, t0=0.0):
-        """Advance U (device tensor) in place by nsteps LSERK4(5) steps."""
-        dU = torch.zeros_like(U)
-        for s in range(nsteps):
-            self.step(U, dU, t0 + s * dt, dt)
+    def run(self, U, nsteps, dt, t0=0.0, graph=True):
+        """Advance U (device tensor) in place by nsteps LSERK4(5) steps
+        (flexi_rk_run: CUDA-graph replay of one step when the operator does not
+        depend on t; graph=False launches every step)."""
+        self._check(U)
+        dU = getattr(self, "_dU", None)
+        if dU is None or dU.shape != U.shape or dU.dtype != U.dtype:
+            dU = self._dU = torch.zeros_like(U)
+        dU.zero_()  # finite: A_1 = 0 multiplies it in the first stage
+        if graph:
+            F.flexi_rk_run(self.ctx, U, dU, nsteps, t0, dt, self._stream())
+        else:
+            for s in range(nsteps):
+                self.step(U, dU, t0 + s * dt, dt)
         return U
 
     def rhs_adjoint(self, U, lam, t=0.0, out=None):
