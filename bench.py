@@ -50,7 +50,7 @@ def peaks():
 # capture time; reported only while the sources are unchanged (else null).
 KERNEL_SOURCES = ["paper_1910_02858_gb300/csrc/k_dg.cuh", "paper_1910_02858_gb300/csrc/dg_common.cuh",
                   "paper_1910_02858_gb300/csrc/k_tc.cuh"]
-NCU_TRAFFIC = {("fp64", "c3f757f9cd658285"): 574510592, ("fp32", "c3f757f9cd658285"): 266318336}
+NCU_TRAFFIC = {("fp64", "2ea14aeed8b9deb4"): 575645952, ("fp32", "2ea14aeed8b9deb4"): 266288128}
 
 
 def kernel_source_hash() -> str:
