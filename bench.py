@@ -461,6 +461,10 @@ def extras(args, s64, U0, mesh, dt, dev, F, wl, Solver, SolverConfig, torch, np)
     except Exception as exc:
         out["lobatto"] = {"error": repr(exc)}
     try:
+        out["c3_32^3_N5"] = c3_forms_pid(dev, F, wl, Solver, SolverConfig, torch)
+    except Exception as exc:
+        out["c3_32^3_N5"] = {"error": repr(exc)}
+    try:
         out["small_cases"] = small_cases_pid(dev, F, wl, Solver, SolverConfig, torch)
     except Exception as exc:
         out["small_cases"] = {"error": repr(exc)}
@@ -506,6 +510,47 @@ def lobatto_pid(mesh, dt, dev, F, wl, Solver, SolverConfig, torch):
             F.flexi_profile(s.ctx, False)
             res[name] = {"pid": ms * 1e6 / (10 * NSTAGES * s.query(F.Q_DOF)), "steps": 10,
                          "lift_vol_ms_per_launch": kt["lift_vol"][0] / max(kt["lift_vol"][1], 1)}
+        finally:
+            s.close()
+    return res
+
+
+def c3_forms_pid(dev, F, wl, Solver, SolverConfig, torch):
+    """The precision form's own workload: Taylor-Green 32^3, N = 5 Gauss (7.08 M DOF),
+    HLLC, in FP64 and the three FP32 forms: PID, whole-step roofline fraction and the
+    relative L2 error against FP64 after 20 steps (momentum against the momentum-vector
+    norm)."""
+    mesh = wl.box_mesh((32, 32, 32), Ngeo=1)
+    N, nsteps = 5, 20
+    U0 = wl.taylor_green(mesh.node_coords(N, 0))
+    res, ref = {}, None
+    for name, prec in (("fp64", F.FP64), ("fp32", F.FP32), ("fp32_tf32x3", F.FP32_TF32), ("fp32_bf16x3", F.FP32_BF16)):
+        s = Solver(SolverConfig(N=N, riemann=F.RIEMANN_HLLC, precision=prec), mesh.coords, mesh.conn, device=dev)
+        try:
+            U = torch.tensor(U0, device=dev, dtype=s.dtype)
+            dt = 0.5 * s.reduce(U)["dt_max"] if ref is None else res["fp64"]["dt"]
+            dU = torch.zeros_like(U)
+            for _ in range(3):
+                s.step(U, dU, 0.0, dt)
+            U = torch.tensor(U0, device=dev, dtype=s.dtype)
+            dU.zero_()
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for k in range(nsteps):
+                s.step(U, dU, k * dt, dt)
+            e1.record()
+            torch.cuda.synchronize(dev)
+            dof = s.query(F.Q_DOF)
+            pid = e0.elapsed_time(e1) * 1e6 / (nsteps * NSTAGES * dof)
+            fpk = FP64_PEAK_TFLOPS if prec == F.FP64 else FP32_PEAK_TFLOPS
+            floor = max(s.query(F.Q_BYTES_PER_STAGE) / dof / peaks().get("hbm_gbs", 6800.0),
+                        s.query(F.Q_FLOPS_PER_STAGE) / dof / (fpk * 1e3))
+            res[name] = {"pid": pid, "step_roofline_frac": floor / pid, "steps": nsteps, "dt": dt}
+            if ref is None:
+                ref = U.double()
+            else:
+                res[name]["rel_l2_err_vs_fp64"] = rel_err_per_var(U, ref)
         finally:
             s.close()
     return res
