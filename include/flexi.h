@@ -29,8 +29,9 @@
  *    reported by the next flexi_reduce or flexi_query(FLEXI_Q_STATUS).
  *  - Errors are returned as flexi_status codes; nothing is thrown across the
  *    ABI and nothing exits the process.  flexi_strerror gives the text.
- *  - No call allocates device memory after flexi_mesh_init, except
- *    flexi_rk_run_host (it uses buffers allocated by flexi_mesh_init too).
+ *  - No call allocates device buffers after flexi_mesh_init (flexi_rk_run_host
+ *    stages through buffers allocated there); flexi_rk_run instantiates a CUDA
+ *    graph, a driver resource, when it first replays a step.
  */
 #ifndef FLEXI_GB300_H
 #define FLEXI_GB300_H
@@ -74,7 +75,7 @@ enum { FLEXI_SPLIT_STANDARD = 0, FLEXI_SPLIT_KEP = 1 };
  * OUTFLOW: the inner state (extrapolation, supersonic outflow);
  * SLIP_WALL: the inner state with its normal velocity reversed (inviscid wall). */
 enum { FLEXI_BC_EXACT = 0, FLEXI_BC_OUTFLOW = 1, FLEXI_BC_SLIP_WALL = 2 };
-/* Exact states for Dirichlet sides (and the manufactured source term). */
+/* Exact states for exact-state boundary sides (and the manufactured source term). */
 enum { FLEXI_EXACT_TGV = 0, FLEXI_EXACT_FREESTREAM = 1, FLEXI_EXACT_MANUFACTURED = 2 };
 
 typedef struct {
@@ -83,7 +84,7 @@ typedef struct {
   int node_type;  /* FLEXI_NODES_* */
   int riemann;    /* FLEXI_RIEMANN_* */
   int precision;  /* FLEXI_FP64 / FLEXI_FP32 / FLEXI_FP32_TF32 / FLEXI_FP32_BF16 */
-  int bc_exact;   /* FLEXI_EXACT_* used on every Dirichlet side */
+  int bc_exact;   /* FLEXI_EXACT_* used on every exact-state (FLEXI_BC_EXACT) side */
   int source;     /* 1: add the manufactured-solution source term */
   int split_form; /* FLEXI_SPLIT_*; FLEXI_SPLIT_KEP needs FLEXI_NODES_LOBATTO and FP64 or FP32 */
   double gamma, Pr, mu; /* ideal gas, constant viscosity (Stokes' hypothesis) */
@@ -97,7 +98,8 @@ typedef struct {
  *           element-local index order [k][j][i].
  *   conn:   HOST pointer, int32 [K][6][3]: (neighbour element, neighbour local
  *           side, orientation code this-side -> neighbour-side), or
- *           (-1 - bc_id, -1, 0) on a Dirichlet boundary side.
+ *           (-1 - bc_id, -1, 0) on a boundary side (kind set by flexi_set_bc;
+ *           exact state by default).
  * Computes on the device: x at the solution nodes, curl-form metrics Ja, 1/J,
  * face normals and surface elements; allocates every buffer later calls use.
  * Returns FLEXI_EMESH for asymmetric connectivity or J <= 0, FLEXI_EINVAL for

@@ -2,7 +2,8 @@
 //
 // Per RK stage (Sec. 5.5 algorithm sequence, re-scheduled for one GPU):
 //   k_prolong   element kernel: U -> primitive face states W(U_face) (a1)
-//   k_bc        boundary sides: Dirichlet state in the outer slot
+//   k_bc        boundary sides: outer state (exact state, outflow or slip wall)
+//   (mortar meshes: k_mortar.cuh interpolates and projects around k_lift_vol and k_face)
 //   k_lift_vol  element kernel: BR1 lifting (a2, a3, Eq. discreteGradient),
 //               gradients to the faces (a4), volume fluxes + contravariant
 //               transform (a6) and the D_hat volume integral (a7)
