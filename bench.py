@@ -474,6 +474,10 @@ def extras(args, s64, U0, mesh, dt, dev, F, wl, Solver, SolverConfig, torch, np)
     except Exception as exc:
         out["c3_32^3_N5"] = {"error": repr(exc)}
     try:
+        out["memory_kib_per_dof"] = memory_per_dof(dev, F, wl, Solver, SolverConfig, torch)
+    except Exception as exc:
+        out["memory_kib_per_dof"] = {"error": repr(exc)}
+    try:
         out["small_cases"] = small_cases_pid(dev, F, wl, Solver, SolverConfig, torch)
     except Exception as exc:
         out["small_cases"] = {"error": repr(exc)}
@@ -565,6 +569,27 @@ def c3_forms_pid(dev, F, wl, Solver, SolverConfig, torch):
     return res
 
 
+def memory_per_dof(dev, F, wl, Solver, SolverConfig, torch):
+    """Device bytes the library holds per DOF (FP64, Gauss, periodic, about 1 M DOF),
+    without and with the adjoint's scratch, plus the caller's U and dU (2 x 5 words),
+    for N = 1..7; the paper measures 1.47, 1.08, 0.906, 0.805, 0.74, 0.693, 0.659 KiB per
+    DOF on its CPUs (Table memoryReq)."""
+    res = {}
+    for N in range(1, 8):
+        nel = max(2, round((1.0e6 ** (1.0 / 3.0)) / (N + 1)))
+        mesh = wl.box_mesh((nel,) * 3, Ngeo=1)
+        row = {"elements": int(mesh.K)}
+        for adj in (False, True):
+            s = Solver(SolverConfig(N=N, riemann=F.RIEMANN_ROE, adjoint=adj), mesh.coords, mesh.conn, device=dev)
+            try:
+                dof = s.query(F.Q_DOF)
+                row["kib_adjoint" if adj else "kib"] = (s.query(F.Q_DEVICE_BYTES) + 2 * 5 * 8 * dof) / dof / 1024
+            finally:
+                s.close()
+        res[f"N{N}"] = row
+    return res
+
+
 def small_cases_pid(dev, F, wl, Solver, SolverConfig, torch):
     """Launch-bound sizes: C1 (4^3, N = 3 LGL, Roe, dt = 1e-3) and the adjoint
     workload's forward (8^3, N = 5, smoothed Roe): PID with every step launched
@@ -640,7 +665,8 @@ def adjoint_ratio(dev, F, wl, Solver, SolverConfig, torch):
     res = {}
     for label, nel, N, nsteps in (("c5_8^3_N5_40steps", 8, 5, 40), ("16^3_N7_10steps", 16, 7, 10)):
         mesh = wl.box_mesh((nel,) * 3, Ngeo=1)
-        s = Solver(SolverConfig(N=N, riemann=F.RIEMANN_ROE_SMOOTH, mu=1 / 400.0), mesh.coords, mesh.conn, device=dev)
+        s = Solver(SolverConfig(N=N, riemann=F.RIEMANN_ROE_SMOOTH, mu=1 / 400.0, adjoint=True), mesh.coords, mesh.conn,
+                   device=dev)
         U0 = torch.tensor(wl.taylor_green(mesh.node_coords(N, 0)), device=dev)
         dt = 1e-3
         lam = torch.randn_like(U0)
@@ -687,8 +713,8 @@ def adjoint_fp32_error(dev, F, wl, Solver, SolverConfig, torch, final_state):
     w3 = np.einsum("k,j,i->kji", w, w, w) * (math.pi / 8) ** 3
     out = {}
     for name, prec, dtype in (("fp64", F.FP64, torch.float64), ("fp32", F.FP32, torch.float32)):
-        s = Solver(SolverConfig(N=N, riemann=F.RIEMANN_ROE_SMOOTH, mu=1 / 400.0, precision=prec), mesh.coords,
-                   mesh.conn, device=dev)
+        s = Solver(SolverConfig(N=N, riemann=F.RIEMANN_ROE_SMOOTH, mu=1 / 400.0, precision=prec, adjoint=True),
+                   mesh.coords, mesh.conn, device=dev)
         try:
             wJ = torch.tensor(w3, device=dev, dtype=dtype)
             U0d = torch.tensor(U0, device=dev, dtype=dtype, requires_grad=True)

@@ -89,6 +89,10 @@ typedef struct {
   int split_form; /* FLEXI_SPLIT_*; FLEXI_SPLIT_KEP needs FLEXI_NODES_LOBATTO and FP64 or FP32 */
   double gamma, Pr, mu; /* ideal gas, constant viscosity (Stokes' hypothesis) */
   double Ma;            /* Mach number of the Taylor-Green exact state */
+  int adjoint;          /* 1: also allocate the discrete adjoint's scratch (volume gradients
+                           and face adjoints, about 37 words per DOF); 0: adjoint calls
+                           return FLEXI_EUNSUPPORTED */
+  int reserved;         /* 0 */
 } flexi_params;
 
 /* Geometry and connectivity (Sec. 3.1 mapping and curl-form metrics, Eq.
@@ -164,9 +168,10 @@ flexi_status flexi_rk_step_stages(flexi_ctx *ctx, void *U, void *dU, double t, d
  *   for k = 5..1: lam_dU += B_k lamU; lamU += dt (dL/dU(U_{k-1}))^T lam_dU;
  *                 lam_dU = A_k lam_dU.
  * U_stages: device [5][K][5][n^3] as written by flexi_rk_step_stages;
- * lamU, lam_dU: device, updated in place.  Requires FLEXI_FP64 or FLEXI_FP32
- * and a Roe-type flux (ROE or ROE_SMOOTH); periodic meshes without source term
- * and with the standard volume integral only (FLEXI_EUNSUPPORTED otherwise). */
+ * lamU, lam_dU: device, updated in place.  Requires flexi_params.adjoint = 1,
+ * FLEXI_FP64 or FLEXI_FP32 and a Roe-type flux (ROE or ROE_SMOOTH); periodic
+ * meshes without source term and with the standard volume integral only
+ * (FLEXI_EUNSUPPORTED otherwise). */
 flexi_status flexi_adjoint_step(flexi_ctx *ctx, const void *U_stages, void *lamU, void *lam_dU, double t,
                                 double dt, void *stream);
 

@@ -561,10 +561,12 @@ flexi_status mesh_init_impl(flexi_ctx* c, const flexi_params* p, int K, const do
     c->m.Ja = c->Ja32; c->m.sJ = c->sJ32; c->m.fgeo = c->fgeo32;
   }
   unsigned char *Wf, *Gf, *Ff, *Utv, *Us, *dUs, *Gvol, *adj;
-  AL(Gvol, (size_t)K * 15 * n3 * rs);
-  c->m.Gvol = Gvol;
-  AL(adj, adjoint_scratch_bytes(c->m, rs));
-  c->adj_scratch = adj;
+  if (p->adjoint) {  // volume gradients of the forward recompute and the reverse sweep's face data
+    AL(Gvol, (size_t)K * 15 * n3 * rs);
+    c->m.Gvol = Gvol;
+    AL(adj, adjoint_scratch_bytes(c->m, rs));
+    c->adj_scratch = adj;
+  }
   AL(Wf, 2 * (size_t)S * NV * n2 * rs);
   AL(Gf, 2 * (size_t)S * 15 * n2 * rs);
   AL(Ff, (size_t)S * NV * n2 * rs);
@@ -708,6 +710,7 @@ flexi_status flexi_mesh_init_mortar(flexi_ctx** out, const flexi_params* p, int 
   if (p->riemann < 0 || p->riemann > 3 || p->bc_exact < 0 || p->bc_exact > 2) return FLEXI_EINVAL;
   if (p->precision < FLEXI_FP64 || p->precision > FLEXI_FP32_BF16) return FLEXI_EINVAL;
   if (p->split_form != FLEXI_SPLIT_STANDARD && p->split_form != FLEXI_SPLIT_KEP) return FLEXI_EINVAL;
+  if (p->adjoint != 0 && p->adjoint != 1) return FLEXI_EINVAL;
   if (p->split_form == FLEXI_SPLIT_KEP &&
       (p->node_type != FLEXI_NODES_LOBATTO || (p->precision != FLEXI_FP64 && p->precision != FLEXI_FP32)))
     return FLEXI_EUNSUPPORTED;
@@ -760,7 +763,7 @@ flexi_status flexi_rk_step_stages(flexi_ctx* c, void* U, void* dU, double t, dou
 }
 
 static bool adjoint_supported(const flexi_ctx* c) {
-  return c->nBC == 0 && c->nMortar == 0 &&
+  return c->p.adjoint && c->nBC == 0 && c->nMortar == 0 &&
          (c->p.riemann == FLEXI_RIEMANN_ROE || c->p.riemann == FLEXI_RIEMANN_ROE_SMOOTH) && !c->p.source &&
          c->p.split_form == FLEXI_SPLIT_STANDARD;
 }

@@ -36,7 +36,8 @@ class flexi_params(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int), ("Ngeo", ctypes.c_int), ("node_type", ctypes.c_int), ("riemann", ctypes.c_int),
                 ("precision", ctypes.c_int), ("bc_exact", ctypes.c_int), ("source", ctypes.c_int),
                 ("split_form", ctypes.c_int), ("gamma", ctypes.c_double), ("Pr", ctypes.c_double),
-                ("mu", ctypes.c_double), ("Ma", ctypes.c_double)]
+                ("mu", ctypes.c_double), ("Ma", ctypes.c_double), ("adjoint", ctypes.c_int),
+                ("reserved2", ctypes.c_int)]
 
 
 class FlexiError(RuntimeError):

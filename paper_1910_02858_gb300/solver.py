@@ -22,6 +22,7 @@ class SolverConfig:
     bc_exact: int = F.EXACT_TGV
     source: bool = False
     split_form: int = F.SPLIT_STANDARD
+    adjoint: bool = False  # allocate the discrete adjoint's scratch
     gamma: float = 1.4
     Pr: float = 0.72
     mu: float = 1.0 / 1600.0
@@ -30,7 +31,8 @@ class SolverConfig:
     def to_c(self) -> F.flexi_params:
         return F.flexi_params(N=self.N, Ngeo=self.Ngeo, node_type=self.node_type, riemann=self.riemann,
                               precision=self.precision, bc_exact=self.bc_exact, source=int(self.source),
-                              split_form=self.split_form, gamma=self.gamma, Pr=self.Pr, mu=self.mu, Ma=self.Ma)
+                              split_form=self.split_form, gamma=self.gamma, Pr=self.Pr, mu=self.mu, Ma=self.Ma,
+                              adjoint=int(self.adjoint))
 
 
 class Solver:

@@ -23,7 +23,7 @@ def _state(mesh, N, seed=2):
                                           (1, 2, (3, 3, 3))])
 def test_rhs_adjoint_vs_oracle(N, riem, nelem):
     mesh = wl.box_mesh(nelem, reorient_seed=N + 1)
-    sk = dict(N=N, riemann=riem, mu=1 / 400.0)
+    sk = dict(N=N, riemann=riem, mu=1 / 400.0, adjoint=True)
     s = _solver(sk, mesh)
     dg = _oracle(sk, mesh)
     U0 = _state(mesh, N)
@@ -39,7 +39,7 @@ def test_rhs_adjoint_vs_oracle(N, riem, nelem):
 def test_adjoint_step_vs_oracle():
     N = 3
     mesh = wl.box_mesh((3, 2, 2), reorient_seed=4)
-    sk = dict(N=N, riemann=2, mu=1 / 400.0)
+    sk = dict(N=N, riemann=2, mu=1 / 400.0, adjoint=True)
     s = _solver(sk, mesh)
     dg = _oracle(sk, mesh)
     U0 = _state(mesh, N)
@@ -63,7 +63,7 @@ def test_dot_product_with_finite_difference_jvp():
     """<lam, J v> from a central difference of flexi_rhs equals <J^T lam, v>."""
     N = 4
     mesh = wl.box_mesh((2, 2, 3), reorient_seed=2)
-    s = _solver(dict(N=N, riemann=2, mu=1 / 400.0), mesh)
+    s = _solver(dict(N=N, riemann=2, mu=1 / 400.0, adjoint=True), mesh)
     U0 = torch.tensor(_state(mesh, N), device=DEV)
     g = torch.Generator(device="cpu").manual_seed(5)
     v = torch.randn(U0.shape, generator=g, dtype=torch.float64).to(DEV)
@@ -82,7 +82,7 @@ def c5():
     40 steps x 5 stages at dt = 1e-3, checkpoints every 20 steps."""
     N = 5
     mesh = wl.box_mesh((8, 8, 8), Ngeo=1)
-    sk = dict(N=N, riemann=2, mu=1 / 400.0)
+    sk = dict(N=N, riemann=2, mu=1 / 400.0, adjoint=True)
     s = _solver(sk, mesh)
     U0 = wl.taylor_green(mesh.node_coords(N, 0))
     yield mesh, s, sk, U0
@@ -175,3 +175,23 @@ def test_c5_fp32_forward_and_adjoint_error(c5):
     assert float((d / r).max()) < 1e-5, (d / r).tolist()
     assert abs(J32 - J64) < 1e-5 * abs(J64)
     assert float((g32 - g64).norm() / g64.norm()) < 1e-5
+
+
+def test_adjoint_needs_its_scratch():
+    """Without flexi_params.adjoint the context holds no adjoint scratch and the
+    adjoint calls report FLEXI_EUNSUPPORTED; with it they run."""
+    from paper_1910_02858_gb300 import flexi as F
+
+    mesh = wl.box_mesh((2, 2, 2))
+    U = torch.tensor(_state(mesh, 2), device=DEV)
+    lam = torch.ones_like(U)
+    s = _solver(dict(N=2, riemann=2, mu=1 / 400.0), mesh)
+    plain = s.query(F.Q_DEVICE_BYTES)
+    with pytest.raises(F.FlexiError) as ei:
+        s.rhs_adjoint(U, lam)
+    s.close()
+    assert ei.value.code == F.FLEXI_EUNSUPPORTED
+    s = _solver(dict(N=2, riemann=2, mu=1 / 400.0, adjoint=True), mesh)
+    assert s.query(F.Q_DEVICE_BYTES) > plain
+    assert torch.isfinite(s.rhs_adjoint(U, lam)).all()
+    s.close()

@@ -165,7 +165,7 @@ def test_mortar_errors():
 
         Solver(SolverConfig(N=2), mesh.coords, mesh.conn, device=DEV)
     assert ei.value.code == F.FLEXI_EMESH
-    s = _solver(dict(N=2, riemann=0), mesh)
+    s = _solver(dict(N=2, riemann=0, adjoint=True), mesh)
     U = torch.tensor(wl.freestream(mesh.node_coords(2, 0)), device=DEV)
     with pytest.raises(F.FlexiError) as ei:
         F.flexi_rhs_adjoint(s.ctx, U, torch.ones_like(U), torch.empty_like(U), 0.0, torch.cuda.current_stream())

@@ -150,7 +150,7 @@ def test_split_unsupported_combinations():
     with pytest.raises(F.FlexiError) as ei:
         _solver(dict(N=3, node_type=1, split_form=2), mesh)
     assert ei.value.code == F.FLEXI_EINVAL
-    s = _solver(dict(N=3, node_type=1, split_form=KEP, riemann=0), mesh)
+    s = _solver(dict(N=3, node_type=1, split_form=KEP, riemann=0, adjoint=True), mesh)
     U = torch.tensor(wl.taylor_green(mesh.node_coords(3, 1)), device=DEV)
     lam = torch.ones_like(U)
     out = torch.empty_like(U)
