@@ -698,7 +698,7 @@ constexpr size_t lift_vol_smem() {
 // a5: numerical flux on every side (master normal)
 // ---------------------------------------------------------------------------
 template <typename real, int n>
-__global__ void __launch_bounds__(128) k_face(const real* __restrict__ Wf, const real* __restrict__ Gf,
+__global__ void __launch_bounds__(128, sizeof(real) == 4 ? 8 : 1) k_face(const real* __restrict__ Wf, const real* __restrict__ Gf,
                                               const real* __restrict__ fgeo, real* __restrict__ Ff, int S, int nBC,
                                               Phys<real> ph) {
   constexpr int n2 = n * n;
@@ -732,7 +732,7 @@ __global__ void __launch_bounds__(128) k_face(const real* __restrict__ Wf, const
 // a8-a10: surface integral, -1/J, RK stage update, face states of the new U
 // ---------------------------------------------------------------------------
 template <typename real, int n, int MODE, bool LGL>
-__global__ void __launch_bounds__(Cfg<n>::T) k_surf(
+__global__ void __launch_bounds__(Cfg<n>::T, (sizeof(real) == 4 && Cfg<n>::T == 512) ? 3 : 2) k_surf(
     const real* __restrict__ Ff, const int* __restrict__ elemSide, const real* __restrict__ sJ,
     const real* __restrict__ Utv, real* __restrict__ U, real* __restrict__ dU, real* __restrict__ Ut,
     real* __restrict__ Wf, const double* __restrict__ xsol, RkStage<real> rk, double t, SourceParams src, int K,
@@ -749,6 +749,21 @@ __global__ void __launch_bounds__(Cfg<n>::T) k_surf(
   const int e = e0 + el;
   const bool valid = e < K;
   const int i = node % n, j = (node / n) % n, k = node / n2;
+  // the node's own global values are requested first, so that their latency
+  // overlaps the gather of the face fluxes and the barrier
+  real vtv[NV], vU[NV], vdU[NV], sj = real(0);
+  if (valid) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const size_t g = ((size_t)e * NV + v) * n3 + node;
+      vtv[v] = Utv[g];
+      if (MODE == 1) {
+        vU[v] = U[g];
+        vdU[v] = dU[g];
+      }
+    }
+    sj = sJ[(size_t)e * n3 + node];
+  }
   load_ops<real, n>(sOp, ops, tid, T);
   for (int t2 = tid; t2 < NE * 6; t2 += T) sES[t2] = (e0 + t2 / 6 < K) ? elemSide[(size_t)e0 * 6 + t2] : 0;
   __syncthreads();
@@ -772,10 +787,9 @@ __global__ void __launch_bounds__(Cfg<n>::T) k_surf(
     const real c0 = lhm[i], c1 = lhp[i], c2 = lhm[j], c3 = lhp[j], c4 = lhm[k], c5 = lhp[k];
     const int pq0 = j + n * k, pq1 = i + n * k, pq2 = i + n * j;
     const real* Fe = sF + el * 6 * NV * n2;
-    const real sj = sJ[(size_t)e * n3 + node];
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      real s = Utv[((size_t)e * NV + v) * n3 + node];
+      real s = vtv[v];
       if (LGL) {  // Gauss-Lobatto: only nodes on a face receive its flux
         if (i == 0) s += c0 * Fe[(0 * NV + v) * n2 + pq0];
         if (i == n - 1) s += c1 * Fe[(1 * NV + v) * n2 + pq0];
@@ -810,8 +824,8 @@ __global__ void __launch_bounds__(Cfg<n>::T) k_surf(
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
         const size_t g = ((size_t)e * NV + v) * n3 + node;
-        const real du = rk.A * dU[g] + rk.dt * ut[v];
-        const real un = U[g] + rk.B * du;
+        const real du = rk.A * vdU[v] + rk.dt * ut[v];
+        const real un = vU[v] + rk.B * du;
         dU[g] = du;
         U[g] = un;
         sU[(el * NV + v) * C::n3p + pidx<n>(i, j, k)] = un;
