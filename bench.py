@@ -560,10 +560,13 @@ def c3_forms_pid(dev, F, wl, Solver, SolverConfig, torch):
             floor = max(s.query(F.Q_BYTES_PER_STAGE) / dof / peaks().get("hbm_gbs", 6800.0),
                         s.query(F.Q_FLOPS_PER_STAGE) / dof / (fpk * 1e3))
             res[name] = {"pid": pid, "step_roofline_frac": floor / pid, "steps": nsteps, "dt": dt}
+            red = s.reduce(U, s.rhs(U))
             if ref is None:
-                ref = U.double()
+                ref, ref_red = U.double(), red
             else:
                 res[name]["rel_l2_err_vs_fp64"] = rel_err_per_var(U, ref)
+                res[name]["ke_rel_err"] = abs(red["kinetic_energy"] - ref_red["kinetic_energy"]) / ref_red["kinetic_energy"]
+                res[name]["dkedt_rel_err"] = abs(red["dkedt"] - ref_red["dkedt"]) / abs(ref_red["dkedt"])
         finally:
             s.close()
     return res

@@ -44,7 +44,10 @@ def test_rhs_fp32_forms_vs_oracle(form, N, nt, riem, nelem):
 
 def test_c3_fp32_forms_100_steps_vs_fp64():
     """C3: TGV 32^3, N = 5, HLLC, 100 steps; every FP32 form within 1e-5 relative
-    L2 per conserved variable of the FP64 path."""
+    L2 per conserved variable of the FP64 path, kinetic energy within 1e-5, and the
+    kinetic-energy dissipation rate dKE/dt within 2e-3.  The rate sum_nodes wJ dKE/dU . U_t
+    is 0.116 while its terms carry the large constant pressure p0 = 71 (low Mach):
+    measured agreement 2e-5 (FP32) to 6e-4 (BF16x3), so 2e-3 leaves a factor 3."""
     N = 5
     mesh = wl.box_mesh((32, 32, 32), Ngeo=1)
     U0 = wl.taylor_green(mesh.node_coords(N, 0))
@@ -53,6 +56,7 @@ def test_c3_fp32_forms_100_steps_vs_fp64():
     dt = s64.reduce(U64)["dt_max"]
     s64.run(U64, 100, dt)
     ke64 = s64.reduce(U64)["kinetic_energy"]
+    rate64 = s64.reduce(U64, s64.rhs(U64))["dkedt"]
     s64.close()
     errs = {}
     for form, prec in FORMS.items():
@@ -65,7 +69,9 @@ def test_c3_fp32_forms_100_steps_vs_fp64():
         errs[form] = (d / r).tolist()
         ke = s.reduce(U)["kinetic_energy"]
         errs[form + "_ke"] = abs(ke - ke64) / ke64
+        errs[form + "_rate"] = abs(s.reduce(U, s.rhs(U))["dkedt"] - rate64) / abs(rate64)
         s.close()
     for form in FORMS:
         assert max(errs[form]) < 1e-5, errs
         assert errs[form + "_ke"] < 1e-5, errs
+        assert errs[form + "_rate"] < 2e-3, errs
