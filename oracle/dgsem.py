@@ -58,6 +58,7 @@ RK_C = [0.0,
         2802321613138.0 / 2924317926251.0]
 
 ROE, HLLC, RUSANOV = 0, 1, 3
+EC = 4  # entropy-conservative surface flux: Chandrashekar's two-point flux in the face normal
 # boundary conditions (Sec. 2.2 names Dirichlet, inflow/outflow and wall conditions, imposed
 # weakly through the outer state of the numerical flux): the outer state U_R is the exact
 # solution, the inner state (outflow: extrapolation), or the inner state with its normal
@@ -77,7 +78,7 @@ class Params:
     Ma: float = 0.1  # for the TGV exact state used as boundary data
     bc_exact: object = eq.EXACT_TGV  # exact function id (or callable (x, t) -> U) on Dirichlet sides
     source: bool = False  # manufactured-solution source term
-    split: str = ""  # "" standard weak form; "pirozzoli" / "central": split form (LGL only)
+    split: str = ""  # "" standard weak form; "pirozzoli" / "chandrashekar" / "central": split form (LGL only)
     bc_kinds: dict = None  # boundary id -> BC_EXACT (default), BC_OUTFLOW, BC_SLIP_WALL
 
 
@@ -95,6 +96,9 @@ class DGSEM:
             return eq.riemann_roe(UL, UR, nv, self.gas, smooth=self.p.smooth_roe)
         if self.p.riemann == RUSANOV:
             return eq.riemann_rusanov(UL, UR, nv, self.gas)
+        if self.p.riemann == EC:
+            return eq.two_point_contravariant(UL, eq.prim(UL, self.gas), UR, eq.prim(UR, self.gas), nv, nv,
+                                              "chandrashekar", self.gas.gamma)
         return eq.riemann_hllc(UL, UR, nv, self.gas)
 
     def rhs(self, U: torch.Tensor, t: float = 0.0, parts: bool = False):
@@ -212,7 +216,8 @@ class DGSEM:
             ax = 3 - l
             ul, wl, jl = Uv.movedim(ax, -2), Wv.movedim(ax, -2), Jl.movedim(ax, -2)  # [..., n(line), 5]
             Fs = eq.two_point_contravariant(ul.unsqueeze(-2), wl.unsqueeze(-2), ul.unsqueeze(-3), wl.unsqueeze(-3),
-                                            jl.unsqueeze(-2), jl.unsqueeze(-3), self.p.split)  # [..., i, a, 5]
+                                            jl.unsqueeze(-2), jl.unsqueeze(-3), self.p.split,
+                                            gas.gamma)  # [..., i, a, 5]
             adv = 2.0 * torch.einsum("ia,...iav->...iv", b.D, Fs)
             vol = vol + adv.movedim(-2, ax).movedim(-1, 1)
             Fvl = sum(Ja[:, l, d].unsqueeze(-1) * Fv[..., d, :] for d in range(3)).movedim(-1, 1)

@@ -188,13 +188,34 @@ def riemann_hllc(UL, UR, n, gas):
 # ---------------------------------------------------------------------------
 
 
-def two_point_contravariant(Ua, Wa, Ub, Wb, Ja_a, Ja_b, kind: str):
+def log_mean(a, b):
+    """Logarithmic mean (a - b) / (ln a - ln b) of positive a, b in the form of
+    Ismail & Roe (2009): with zeta = a/b, f = (zeta - 1)/(zeta + 1) and u = f^2,
+    ln(zeta) = 2 atanh(f), so the mean is (a + b) / (2 F) with F = atanh(f)/f =
+    ln(zeta)/(2 f).  For u < 1e-2 (where the quotient loses digits) F is the series
+    sum_k u^k / (2k + 1), kept to u^7 (the next term is below 1e-17)."""
+    zeta = a / b
+    f = (zeta - 1.0) / (zeta + 1.0)
+    u = f * f
+    series = torch.zeros_like(u)
+    for k in range(7, -1, -1):
+        series = series * u + 1.0 / (2 * k + 1)
+    safe_f = torch.where(u < 1e-2, torch.ones_like(f), f)
+    F = torch.where(u < 1e-2, series, torch.log(zeta) / (2.0 * safe_f))
+    return (a + b) / (2.0 * F)
+
+
+def two_point_contravariant(Ua, Wa, Ub, Wb, Ja_a, Ja_b, kind: str, gamma: float = 1.4):
     """Contravariant two-point flux sum_d F#_d(U_a, U_b) * (Ja_d(a) + Ja_d(b)) / 2.
 
     kind "pirozzoli": kinetic-energy-preserving flux of Pirozzoli (2011), the one
     of the paper's NACA 64418 computation (Sec. 7.1): with arithmetic means {.},
     F#_rho = {rho}{u_d}, F#_m = {rho}{u_d}{u} + {p} e_d, F#_E = {rho}{u_d}{H},
-    H = (rho E + p) / rho.  kind "central": (F(U_a) + F(U_b)) / 2 (standard DG).
+    H = (rho E + p) / rho.  kind "chandrashekar": the entropy-conservative flux of
+    Chandrashekar (2013) with beta = rho / (2 p), logarithmic means rho_ln, beta_ln:
+    F#_rho = rho_ln {u_d}, F#_m = F#_rho {u} + ({rho} / (2 {beta})) e_d,
+    F#_E = F#_rho (1 / (2 (gamma - 1) beta_ln) - {|u|^2} / 2) + {u} . F#_m.
+    kind "central": (F(U_a) + F(U_b)) / 2 (standard DG).
     Variables last; Ja_* are [..., 3] (the row Ja^l_. of the sweep direction l).
     """
     Jm = 0.5 * (Ja_a + Ja_b)
@@ -202,6 +223,16 @@ def two_point_contravariant(Ua, Wa, Ub, Wb, Ja_a, Ja_b, kind: str):
         Fa = flux_conv(Ua, Wa)  # [..., 3, 5]
         Fb = flux_conv(Ub, Wb)
         return 0.5 * ((Fa + Fb) * Jm.unsqueeze(-1)).sum(-2)
+    if kind == "chandrashekar":
+        ra, rb = Wa[..., 0], Wb[..., 0]
+        ba, bb = ra / (2.0 * Wa[..., 4]), rb / (2.0 * Wb[..., 4])
+        vel = 0.5 * (Wa[..., 1:4] + Wb[..., 1:4])
+        q2 = 0.5 * ((Wa[..., 1:4] ** 2).sum(-1) + (Wb[..., 1:4] ** 2).sum(-1))
+        ptil = 0.5 * (ra + rb) / (ba + bb)
+        frho = log_mean(ra, rb) * (vel * Jm).sum(-1)
+        fm = frho.unsqueeze(-1) * vel + ptil.unsqueeze(-1) * Jm
+        fE = frho * (1.0 / (2.0 * (gamma - 1.0) * log_mean(ba, bb)) - 0.5 * q2) + (vel * fm).sum(-1)
+        return torch.cat([frho.unsqueeze(-1), fm, fE.unsqueeze(-1)], dim=-1)
     rho = 0.5 * (Wa[..., 0] + Wb[..., 0])
     vel = 0.5 * (Wa[..., 1:4] + Wb[..., 1:4])
     p = 0.5 * (Wa[..., 4] + Wb[..., 4])
