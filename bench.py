@@ -499,7 +499,8 @@ def lobatto_pid(mesh, dt, dev, F, wl, Solver, SolverConfig, torch):
     res = {}
     x = mesh.node_coords(7, 1)
     for name, prec, split in (("fp64", F.FP64, F.SPLIT_STANDARD), ("fp32", F.FP32, F.SPLIT_STANDARD),
-                              ("fp64_split_kep", F.FP64, F.SPLIT_KEP), ("fp32_split_kep", F.FP32, F.SPLIT_KEP)):
+                              ("fp64_split_kep", F.FP64, F.SPLIT_KEP), ("fp32_split_kep", F.FP32, F.SPLIT_KEP),
+                              ("fp64_split_ec", F.FP64, F.SPLIT_EC), ("fp32_split_ec", F.FP32, F.SPLIT_EC)):
         s = Solver(SolverConfig(N=7, node_type=F.NODES_LOBATTO, riemann=F.RIEMANN_HLLC, precision=prec,
                                 split_form=split), mesh.coords, mesh.conn, device=dev)
         try:

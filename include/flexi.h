@@ -58,7 +58,8 @@ enum { FLEXI_NODES_GAUSS = 0, FLEXI_NODES_LOBATTO = 1 };
 /* Riemann solvers (Sec. 2.2 names Roe, HLL-type and Rusanov fluxes): ROE_SMOOTH
  * replaces |lambda| by (lambda^2 + delta^2)/(2 delta) below delta = 0.1 c (C^1
  * operator); RUSANOV is the local Lax-Friedrichs flux. */
-enum { FLEXI_RIEMANN_ROE = 0, FLEXI_RIEMANN_HLLC = 1, FLEXI_RIEMANN_ROE_SMOOTH = 2, FLEXI_RIEMANN_RUSANOV = 3 };
+enum { FLEXI_RIEMANN_ROE = 0, FLEXI_RIEMANN_HLLC = 1, FLEXI_RIEMANN_ROE_SMOOTH = 2, FLEXI_RIEMANN_RUSANOV = 3,
+       FLEXI_RIEMANN_EC = 4 /* entropy conservative: the EC two-point flux below, no dissipation */ };
 /* Arithmetic forms: FP64; FP32 storage+flux math with FP32 line sweeps; FP32
  * with the D-matrix line sweeps on tensor cores in TF32 or BF16, each operand
  * split into three terms of the narrow type (six products, FP32 accumulation). */
@@ -67,8 +68,11 @@ enum { FLEXI_FP64 = 0, FLEXI_FP32 = 1, FLEXI_FP32_TF32 = 2, FLEXI_FP32_BF16 = 3 
  * the split form of Eq. semiDiscreteSplit on Gauss-Lobatto nodes, 2 sum_a D_ia
  * F#(U_i, U_a) with Pirozzoli's kinetic-energy-preserving two-point flux (the
  * flux of the paper's NACA 64418 computation, Sec. 7.1) and metric terms averaged
- * over each pair; viscous fluxes stay in the standard form. */
-enum { FLEXI_SPLIT_STANDARD = 0, FLEXI_SPLIT_KEP = 1 };
+ * over each pair; EC uses Chandrashekar's entropy-conservative two-point flux
+ * (logarithmic means of rho and beta = rho/(2p)) instead; with FLEXI_RIEMANN_EC at
+ * the faces and mu = 0 the discrete entropy is conserved.  Viscous fluxes stay in
+ * the standard form. */
+enum { FLEXI_SPLIT_STANDARD = 0, FLEXI_SPLIT_KEP = 1, FLEXI_SPLIT_EC = 2 };
 /* Boundary kinds (Sec. 2.2: boundary conditions enter weakly through the outer
  * state of the numerical flux; the inner lifted gradients are used outside):
  * EXACT: the exact state FLEXI_EXACT_* at the face nodes (Dirichlet; the default);
@@ -86,7 +90,7 @@ typedef struct {
   int precision;  /* FLEXI_FP64 / FLEXI_FP32 / FLEXI_FP32_TF32 / FLEXI_FP32_BF16 */
   int bc_exact;   /* FLEXI_EXACT_* used on every exact-state (FLEXI_BC_EXACT) side */
   int source;     /* 1: add the manufactured-solution source term */
-  int split_form; /* FLEXI_SPLIT_*; FLEXI_SPLIT_KEP needs FLEXI_NODES_LOBATTO and FP64 or FP32 */
+  int split_form; /* FLEXI_SPLIT_*; KEP and EC need FLEXI_NODES_LOBATTO and FP64 or FP32 */
   double gamma, Pr, mu; /* ideal gas, constant viscosity (Stokes' hypothesis) */
   double Ma;            /* Mach number of the Taylor-Green exact state */
   int adjoint;          /* 1: also allocate the discrete adjoint's scratch (volume gradients

@@ -306,12 +306,72 @@ __device__ __forceinline__ void riemann_rusanov(const real WL[NV], const real WR
 }
 
 template <typename real>
+__device__ __forceinline__ real dg_log(real x);
+template <>
+__device__ __forceinline__ double dg_log<double>(double x) { return log(x); }
+template <>
+__device__ __forceinline__ float dg_log<float>(float x) { return logf(x); }
+
+// logarithmic mean (a - b)/(ln a - ln b) of positive a, b (Ismail & Roe form):
+// zeta = a/b, f = (zeta - 1)/(zeta + 1), u = f^2; mean = (a + b)/(2 F) with
+// F = atanh(f)/f = ln(zeta)/(2 f), or its series sum_k u^k/(2k + 1) to u^7 for u < 1e-2
+template <typename real>
+__device__ __forceinline__ real log_mean(real a, real b) {
+  const real zeta = a / b;
+  const real f = (zeta - real(1)) / (zeta + real(1));
+  const real u = f * f;
+  real F;
+  if (u < real(1e-2)) {
+    F = real(1.0 / 15.0);
+    F = F * u + real(1.0 / 13.0);
+    F = F * u + real(1.0 / 11.0);
+    F = F * u + real(1.0 / 9.0);
+    F = F * u + real(1.0 / 7.0);
+    F = F * u + real(1.0 / 5.0);
+    F = F * u + real(1.0 / 3.0);
+    F = F * u + real(1);
+  } else {
+    F = dg_log(zeta) / (real(2) * f);
+  }
+  return (a + b) / (real(2) * F);
+}
+
+// Chandrashekar's entropy-conservative two-point flux in the direction Jm (the
+// averaged metric row, or the face normal), from the two sides' rho, velocity,
+// beta = rho/(2p) and |u|^2:  f_rho = rho_ln {u}.Jm, f_m = f_rho {u} + ({rho}/(2{beta})) Jm,
+// f_E = f_rho (1/(2(gamma-1) beta_ln) - {|u|^2}/2) + {u}.f_m
+template <typename real>
+__device__ __forceinline__ void ec_flux(real ra, const real ua[3], real ba, real qa, real rb, const real ub[3],
+                                        real bb, real qb, const real Jm[3], const Phys<real>& ph, real f[NV]) {
+  const real um[3] = {real(0.5) * (ua[0] + ub[0]), real(0.5) * (ua[1] + ub[1]), real(0.5) * (ua[2] + ub[2])};
+  const real frho = log_mean(ra, rb) * (um[0] * Jm[0] + um[1] * Jm[1] + um[2] * Jm[2]);
+  const real ptil = real(0.5) * (ra + rb) / (ba + bb);
+  f[0] = frho;
+  f[1] = frho * um[0] + ptil * Jm[0];
+  f[2] = frho * um[1] + ptil * Jm[1];
+  f[3] = frho * um[2] + ptil * Jm[2];
+  f[4] = frho * (real(0.5) * ph.inv_gm1 / log_mean(ba, bb) - real(0.25) * (qa + qb)) + um[0] * f[1] + um[1] * f[2] +
+         um[2] * f[3];
+}
+
+// entropy-conservative surface flux: ec_flux between the face states in the normal n
+template <typename real>
+__device__ __forceinline__ void riemann_ec(const real WL[NV], const real WR[NV], const real n[3], const Phys<real>& ph,
+                                           real f[NV]) {
+  const real uL[3] = {WL[1], WL[2], WL[3]}, uR[3] = {WR[1], WR[2], WR[3]};
+  ec_flux(WL[0], uL, real(0.5) * WL[0] / WL[4], uL[0] * uL[0] + uL[1] * uL[1] + uL[2] * uL[2], WR[0], uR,
+          real(0.5) * WR[0] / WR[4], uR[0] * uR[0] + uR[1] * uR[1] + uR[2] * uR[2], n, ph, f);
+}
+
+template <typename real>
 __device__ __forceinline__ void riemann(const real WL[NV], const real WR[NV], const real n[3],
                                         const Phys<real>& ph, real f[NV]) {
   if (ph.riemann == 1)
     riemann_hllc(WL, WR, n, ph, f);
   else if (ph.riemann == 3)
     riemann_rusanov(WL, WR, n, ph, f);
+  else if (ph.riemann == 4)
+    riemann_ec(WL, WR, n, ph, f);
   else
     riemann_roe(WL, WR, n, ph, ph.riemann == 2, f);
 }

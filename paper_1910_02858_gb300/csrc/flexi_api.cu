@@ -547,7 +547,7 @@ flexi_status mesh_init_impl(flexi_ctx* c, const flexi_params* p, int K, const do
   c->m.status = c->status;
   c->m.sweep_mode = p->precision == FLEXI_FP32_TF32 ? 1 : (p->precision == FLEXI_FP32_BF16 ? 2 : 0);
   c->m.lgl = p->node_type == FLEXI_NODES_LOBATTO ? 1 : 0;
-  c->m.split = p->split_form == FLEXI_SPLIT_KEP ? 1 : 0;
+  c->m.split = p->split_form;
   const size_t rs = c->rs;
   if (c->fp64) {
     c->m.Ja = c->Ja64; c->m.sJ = c->sJ64; c->m.fgeo = c->fgeo64;
@@ -707,11 +707,11 @@ flexi_status flexi_mesh_init_mortar(flexi_ctx** out, const flexi_params* p, int 
   if (p->N < 1 || p->N > 7) return p->N > 7 ? FLEXI_EUNSUPPORTED : FLEXI_EINVAL;
   if (p->Ngeo < 1 || p->Ngeo > p->N) return FLEXI_EINVAL;
   if (p->node_type != FLEXI_NODES_GAUSS && p->node_type != FLEXI_NODES_LOBATTO) return FLEXI_EINVAL;
-  if (p->riemann < 0 || p->riemann > 3 || p->bc_exact < 0 || p->bc_exact > 2) return FLEXI_EINVAL;
+  if (p->riemann < 0 || p->riemann > 4 || p->bc_exact < 0 || p->bc_exact > 2) return FLEXI_EINVAL;
   if (p->precision < FLEXI_FP64 || p->precision > FLEXI_FP32_BF16) return FLEXI_EINVAL;
-  if (p->split_form != FLEXI_SPLIT_STANDARD && p->split_form != FLEXI_SPLIT_KEP) return FLEXI_EINVAL;
+  if (p->split_form < FLEXI_SPLIT_STANDARD || p->split_form > FLEXI_SPLIT_EC) return FLEXI_EINVAL;
   if (p->adjoint != 0 && p->adjoint != 1) return FLEXI_EINVAL;
-  if (p->split_form == FLEXI_SPLIT_KEP &&
+  if (p->split_form != FLEXI_SPLIT_STANDARD &&
       (p->node_type != FLEXI_NODES_LOBATTO || (p->precision != FLEXI_FP64 && p->precision != FLEXI_FP32)))
     return FLEXI_EUNSUPPORTED;
   if (!(p->gamma > 1.0) || !(p->Pr > 0.0) || !(p->mu >= 0.0)) return FLEXI_EINVAL;

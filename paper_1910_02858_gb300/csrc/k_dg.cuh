@@ -271,9 +271,10 @@ __global__ void k_bc(const double* __restrict__ xbc, const int* __restrict__ bcK
 // a2-a4, a6, a7: lifting, gradient prolongation, volume integral
 // ---------------------------------------------------------------------------
 // SW: 0 line sweeps on the FP32/FP64 pipes; 1 TF32 and 2 BF16 3-term split mma (float only).
-// SPLIT (Gauss-Lobatto, SW = 0 only): the split-form volume integral of Sec. 3.3
+// SPLIT (Gauss-Lobatto, SW = 0 only): the split-form volume integral of Sec. 3.3 with the
+// kinetic-energy-preserving flux (1) or the entropy-conservative flux (2)
 // (Eq. semiDiscreteSplit) with the kinetic-energy-preserving two-point flux.
-template <typename real, int n, int SW, bool LGL, bool SPLIT = false>
+template <typename real, int n, int SW, bool LGL, int SPLIT = 0>
 __global__ void __launch_bounds__(Cfg<n>::T) k_lift_vol(
     const real* __restrict__ U, const real* __restrict__ Ja, const real* __restrict__ sJ,
     const real* __restrict__ Wf, const real* __restrict__ fgeo, const int* __restrict__ elemSide,
@@ -501,12 +502,14 @@ __global__ void __launch_bounds__(Cfg<n>::T) k_lift_vol(
       for (int v = 0; v < NV; ++v) acc[v] = sOut[(el * NV + v) * n3p + pn];
     }
     __syncthreads();
-    // Advective part: 2 sum_a D_{i_l a} Fcal#^l(node, node with index_l = a) with the
-    // kinetic-energy-preserving flux of Pirozzoli and metric terms averaged over the
-    // pair.  Staged per node: rho, u, v, w, p, H = (rho E + p)/rho, Ja (9).
+    // Advective part: 2 sum_a D_{i_l a} Fcal#^l(node, node with index_l = a) with
+    // metric terms averaged over the pair.  Staged per node: rho, u, v, w, then
+    // p, H = (rho E + p)/rho (kinetic-energy preserving, Pirozzoli) or
+    // beta = rho/(2p), |u|^2 (entropy conservative, Chandrashekar), and Ja (9).
 #pragma unroll
-    for (int c = 0; c < NV; ++c) myb[c * n3p + pn] = W[c];
-    const real H = (Uo[4] + W[4]) / W[0];
+    for (int c = 0; c < 4; ++c) myb[c * n3p + pn] = W[c];
+    const real H = SPLIT == 2 ? W[1] * W[1] + W[2] * W[2] + W[3] * W[3] : (Uo[4] + W[4]) / W[0];
+    myb[4 * n3p + pn] = SPLIT == 2 ? real(0.5) * W[0] / W[4] : W[4];
     myb[5 * n3p + pn] = H;
 #pragma unroll
     for (int c = 0; c < 9; ++c) myb[(6 + c) * n3p + pn] = jac[c];
@@ -526,21 +529,31 @@ __global__ void __launch_bounds__(Cfg<n>::T) k_lift_vol(
         for (int a = 0; a < n; ++a) {
           const int pa = l == 0 ? pidx<n>(a, j, k) : (l == 1 ? pidx<n>(i, a, k) : pidx<n>(i, j, a));
           const real* f = myb + pa;
-          const real rs = W[0] + f[0], us = W[1] + f[n3p], vs = W[2] + f[2 * n3p], ws = W[3] + f[3 * n3p];
-          const real ps = W[4] + f[4 * n3p], Hs = H + f[5 * n3p];
-          const real j0 = J0 + f[(6 + 3 * l) * n3p], j1 = J1 + f[(7 + 3 * l) * n3p], j2 = J2 + f[(8 + 3 * l) * n3p];
-          const real m = real(0.125) * rs * (us * j0 + vs * j1 + ws * j2);
           const real d = sD[a * n + il];
-          const real dm = d * m, dp = real(0.5) * d * ps;
-          sm[0] += dm;
-          sm[1] += dm * us + dp * j0;
-          sm[2] += dm * vs + dp * j1;
-          sm[3] += dm * ws + dp * j2;
-          sm[4] += dm * Hs;
-        }
-        acc[0] += real(2) * sm[0];
+          if constexpr (SPLIT == 2) {
+            const real ua[3] = {W[1], W[2], W[3]}, ub[3] = {f[n3p], f[2 * n3p], f[3 * n3p]};
+            const real Jm[3] = {real(0.5) * (J0 + f[(6 + 3 * l) * n3p]), real(0.5) * (J1 + f[(7 + 3 * l) * n3p]),
+                                real(0.5) * (J2 + f[(8 + 3 * l) * n3p])};
+            real F[NV];
+            ec_flux(W[0], ua, real(0.5) * W[0] / W[4], H, f[0], ub, f[4 * n3p], f[5 * n3p], Jm, ph, F);
 #pragma unroll
-        for (int v = 1; v < NV; ++v) acc[v] += sm[v];
+            for (int v = 0; v < NV; ++v) sm[v] += real(2) * d * F[v];
+          } else {
+            const real rs = W[0] + f[0], us = W[1] + f[n3p], vs = W[2] + f[2 * n3p], ws = W[3] + f[3 * n3p];
+            const real ps = W[4] + f[4 * n3p], Hs = H + f[5 * n3p];
+            const real j0 = J0 + f[(6 + 3 * l) * n3p], j1 = J1 + f[(7 + 3 * l) * n3p],
+                       j2 = J2 + f[(8 + 3 * l) * n3p];
+            const real m = real(0.125) * rs * (us * j0 + vs * j1 + ws * j2);
+            const real dm = d * m, dp = real(0.5) * d * ps;
+            sm[0] += real(2) * dm;
+            sm[1] += dm * us + dp * j0;
+            sm[2] += dm * vs + dp * j1;
+            sm[3] += dm * ws + dp * j2;
+            sm[4] += dm * Hs;
+          }
+        }
+#pragma unroll
+        for (int v = 0; v < NV; ++v) acc[v] += sm[v];
       }
     } else {
       // One thread per (direction l, line): F# is symmetric, so every pair (i, a),
@@ -564,7 +577,8 @@ __global__ void __launch_bounds__(Cfg<n>::T) k_lift_vol(
         for (int ii = 0; ii < n; ++ii)
 #pragma unroll
           for (int c = 0; c < NV; ++c) o[c * n3p + ii * stride] = real(0);
-#pragma unroll
+        // (the entropy-conservative pair flux is long: keep its loops rolled)
+#pragma unroll(SPLIT == 2 ? 1 : n)
         for (int ii = 0; ii < n; ++ii) {
           const real* fi = f + ii * stride;
           const real ri = fi[0], ui = fi[n3p], vi = fi[2 * n3p], wi = fi[3 * n3p], pi = fi[4 * n3p];
@@ -574,26 +588,44 @@ __global__ void __launch_bounds__(Cfg<n>::T) k_lift_vol(
           for (int c = 0; c < NV; ++c) ai[c] = real(0);
           if (ii == 0 || ii == n - 1) {  // 2 D_ii F#(i, i) = 2 D_ii Fcal^{c,l}(U_i)
             const real dd = real(2) * sD[ii * n + ii];
-            const real uc = ui * ji0 + vi * ji1 + wi * ji2;
-            const real m = dd * ri * uc;
-            ai[0] = m;
-            ai[1] = m * ui + dd * pi * ji0;
-            ai[2] = m * vi + dd * pi * ji1;
-            ai[3] = m * wi + dd * pi * ji2;
-            ai[4] = m * Hi;
-          }
+            if constexpr (SPLIT == 2) {
+              const real u3[3] = {ui, vi, wi}, J3[3] = {ji0, ji1, ji2};
+              real F[NV];
+              ec_flux(ri, u3, pi, Hi, ri, u3, pi, Hi, J3, ph, F);
 #pragma unroll
+              for (int c = 0; c < NV; ++c) ai[c] = dd * F[c];
+            } else {
+              const real uc = ui * ji0 + vi * ji1 + wi * ji2;
+              const real m = dd * ri * uc;
+              ai[0] = m;
+              ai[1] = m * ui + dd * pi * ji0;
+              ai[2] = m * vi + dd * pi * ji1;
+              ai[3] = m * wi + dd * pi * ji2;
+              ai[4] = m * Hi;
+            }
+          }
+#pragma unroll(SPLIT == 2 ? 1 : n)
           for (int aa = ii + 1; aa < n; ++aa) {
             const real* fa = f + aa * stride;
-            // pair sums (twice the arithmetic means)
-            const real rs = ri + fa[0], us = ui + fa[n3p], vs = vi + fa[2 * n3p], ws = wi + fa[3 * n3p];
-            const real ps = pi + fa[4 * n3p], Hs = Hi + fa[5 * n3p];
-            const real j0 = ji0 + fa[jo], j1 = ji1 + fa[jo + n3p], j2 = ji2 + fa[jo + 2 * n3p];
-            const real m = real(0.125) * rs * (us * j0 + vs * j1 + ws * j2);  // {rho} {u . Ja^l}
-            const real hp = real(0.5) * ps;
-            // 2 F#: mass 2 m; momentum m u_s + (p_s / 2) Ja_s; energy m H_s
-            const real F0 = real(2) * m, F1 = m * us + hp * j0, F2 = m * vs + hp * j1, F3 = m * ws + hp * j2;
-            const real F4 = m * Hs;
+            real F0, F1, F2, F3, F4;  // 2 F#(i, a)
+            if constexpr (SPLIT == 2) {
+              const real u3[3] = {ui, vi, wi}, ua3[3] = {fa[n3p], fa[2 * n3p], fa[3 * n3p]};
+              const real Jm[3] = {real(0.5) * (ji0 + fa[jo]), real(0.5) * (ji1 + fa[jo + n3p]),
+                                  real(0.5) * (ji2 + fa[jo + 2 * n3p])};
+              real F[NV];
+              ec_flux(ri, u3, pi, Hi, fa[0], ua3, fa[4 * n3p], fa[5 * n3p], Jm, ph, F);
+              F0 = real(2) * F[0]; F1 = real(2) * F[1]; F2 = real(2) * F[2]; F3 = real(2) * F[3]; F4 = real(2) * F[4];
+            } else {
+              // pair sums (twice the arithmetic means)
+              const real rs = ri + fa[0], us = ui + fa[n3p], vs = vi + fa[2 * n3p], ws = wi + fa[3 * n3p];
+              const real ps = pi + fa[4 * n3p], Hs = Hi + fa[5 * n3p];
+              const real j0 = ji0 + fa[jo], j1 = ji1 + fa[jo + n3p], j2 = ji2 + fa[jo + 2 * n3p];
+              const real m = real(0.125) * rs * (us * j0 + vs * j1 + ws * j2);  // {rho} {u . Ja^l}
+              const real hp = real(0.5) * ps;
+              // 2 F#: mass 2 m; momentum m u_s + (p_s / 2) Ja_s; energy m H_s
+              F0 = real(2) * m; F1 = m * us + hp * j0; F2 = m * vs + hp * j1; F3 = m * ws + hp * j2;
+              F4 = m * Hs;
+            }
             const real dia = sD[aa * n + ii], dai = sD[ii * n + aa];
             ai[0] += dia * F0; ai[1] += dia * F1; ai[2] += dia * F2; ai[3] += dia * F3; ai[4] += dia * F4;
             real* oa = o + aa * stride;
@@ -684,7 +716,7 @@ __global__ void __launch_bounds__(Cfg<n>::T) k_lift_vol(
   }
 }
 
-template <typename real, int n, int SW, bool SPLIT = false>
+template <typename real, int n, int SW, int SPLIT = 0>
 constexpr size_t lift_vol_smem() {
   using C = Cfg<n>;
   // the FP64 form sweeps per node and needs no result buffer
@@ -884,7 +916,7 @@ cudaError_t launch_bc(const DevMesh& m, double t, const Phys<real>& ph, cudaStre
   return cudaGetLastError();
 }
 
-template <typename real, int n, int SW, bool LGL = false, bool SPLIT = false>
+template <typename real, int n, int SW, bool LGL = false, int SPLIT = 0>
 static cudaError_t lift_vol_n(const DevMesh& m, const real* U, const Ops<real>& ops, const Phys<real>& ph,
                               int store_grad, cudaStream_t st) {
   using C = Cfg<n>;
@@ -916,8 +948,11 @@ cudaError_t launch_lift_vol(const DevMesh& m, const real* U, const Ops<real>& op
       FLEXI_DISPATCH_N(m.n, return lift_vol_n<real, NN, 2>(m, U, ops, ph, store_grad, st));
     }
   }
-  if (m.lgl && m.split) {
-    FLEXI_DISPATCH_N(m.n, return lift_vol_n<real, NN, 0, true, true>(m, U, ops, ph, store_grad, st));
+  if (m.lgl && m.split == 1) {
+    FLEXI_DISPATCH_N(m.n, return lift_vol_n<real, NN, 0, true, 1>(m, U, ops, ph, store_grad, st));
+  }
+  if (m.lgl && m.split == 2) {
+    FLEXI_DISPATCH_N(m.n, return lift_vol_n<real, NN, 0, true, 2>(m, U, ops, ph, store_grad, st));
   }
   if (m.lgl) {
     FLEXI_DISPATCH_N(m.n, return lift_vol_n<real, NN, 0, true>(m, U, ops, ph, store_grad, st));

@@ -16,10 +16,10 @@ LIB_PATH = os.path.join(HERE, "libflexi_gb300.so")
 
 FLEXI_OK, FLEXI_EINVAL, FLEXI_ENOMEM, FLEXI_ECUDA, FLEXI_EMESH, FLEXI_ENONPHYSICAL, FLEXI_EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
 NODES_GAUSS, NODES_LOBATTO = 0, 1
-RIEMANN_ROE, RIEMANN_HLLC, RIEMANN_ROE_SMOOTH, RIEMANN_RUSANOV = 0, 1, 2, 3
+RIEMANN_ROE, RIEMANN_HLLC, RIEMANN_ROE_SMOOTH, RIEMANN_RUSANOV, RIEMANN_EC = 0, 1, 2, 3, 4
 FP64, FP32, FP32_TF32, FP32_BF16 = 0, 1, 2, 3
 EXACT_TGV, EXACT_FREESTREAM, EXACT_MANUFACTURED = 0, 1, 2
-SPLIT_STANDARD, SPLIT_KEP = 0, 1
+SPLIT_STANDARD, SPLIT_KEP, SPLIT_EC = 0, 1, 2
 CONN_MORTAR = -(1 << 30)
 BC_EXACT, BC_OUTFLOW, BC_SLIP_WALL = 0, 1, 2
 Q_K, Q_N, Q_NSIDES, Q_NBCSIDES, Q_DOF, Q_BYTES_PER_STAGE, Q_FLOPS_PER_STAGE, Q_STATUS, Q_DEVICE_BYTES, Q_PRECISION = range(10)

@@ -21,7 +21,7 @@ import torch
 
 import workloads as wl
 from oracle import equations as eq
-from oracle.dgsem import DGSEM, HLLC, ROE, RUSANOV, Params
+from oracle.dgsem import DGSEM, EC, HLLC, ROE, RUSANOV, Params
 
 pytestmark = pytest.mark.gpu
 
@@ -45,13 +45,14 @@ def _solver(cfg_kw, mesh):
 
 
 def _oracle(cfg_kw, mesh):
-    r = {0: ROE, 1: HLLC, 2: ROE, 3: RUSANOV}[cfg_kw.get("riemann", 0)]
+    r = {0: ROE, 1: HLLC, 2: ROE, 3: RUSANOV, 4: EC}[cfg_kw.get("riemann", 0)]
     bc = cfg_kw.get("bc_exact", 0)
     return DGSEM(Params(N=cfg_kw["N"], node_type=cfg_kw.get("node_type", 0), riemann=r,
                         smooth_roe=cfg_kw.get("riemann", 0) == 2, mu=cfg_kw.get("mu", 1 / 1600.0),
                         Ma=cfg_kw.get("Ma", 0.1), bc_exact=bc, source=cfg_kw.get("source", False),
                         gamma=cfg_kw.get("gamma", 1.4), Pr=cfg_kw.get("Pr", 0.72),
-                        split="pirozzoli" if cfg_kw.get("split_form", 0) == 1 else ""), mesh.coords, mesh.conn)
+                        split={0: "", 1: "pirozzoli", 2: "chandrashekar"}[cfg_kw.get("split_form", 0)]),
+                 mesh.coords, mesh.conn)
 
 
 def rounding_sensitivity(dg, U0, t, trials=2, mesh=None):
