@@ -80,6 +80,8 @@ class Params:
     source: bool = False  # manufactured-solution source term
     split: str = ""  # "" standard weak form; "pirozzoli" / "chandrashekar" / "central": split form (LGL only)
     bc_kinds: dict = None  # boundary id -> BC_EXACT (default), BC_OUTFLOW, BC_SLIP_WALL
+    lifting: str = "br1"  # "br1" (Eq. discreteGradient) or "br2" (face gradients of Bassi & Rebay 1997)
+    eta_br2: float = 2.0  # BR2 penalty factor on a face's own lifting
 
 
 class DGSEM:
@@ -153,7 +155,10 @@ class DGSEM:
         G = torch.stack(grads, dim=1)  # [K, 3 (d), 5, n,n,n]
 
         # a4: gradients on the faces
-        Gf = geo.face_values(G.flatten(1, 2), b.l_side)  # [K,6,15,q,p]
+        if self.p.lifting == "br2":
+            Gf = self._br2_face_gradients(G, Wf, Qf)
+        else:
+            Gf = geo.face_values(G.flatten(1, 2), b.l_side)  # [K,6,15,q,p]
         GL, GR = geo.master_slave(Gf)
         if len(bnd) > 0:
             GR = GR.clone()
@@ -194,6 +199,31 @@ class DGSEM:
         if parts:
             return Ut, dict(W=W, G=G, fstar=fstar, vol=vol, surf=surf, Wstar=Wstar, UL=UL, UR=UR, GL=GL, GR=GR)
         return Ut
+
+    def _br2_face_gradients(self, G, Wf, Qf):
+        """BR2 face gradients (Bassi & Rebay 1997; the paper names BR2 without formulas).
+        Reading: the BR1 gradient G of Eq. discreteGradient is the broken gradient plus the
+        lifting r_f of every face, r_f = (1/J) l_hat(+-1) (U* - U_e) n s_hat spread along the
+        face's direction, with U_e the element's own face state and n s_hat its own outward
+        metric (Ja^l . N).  On each side of a face the viscous flux takes
+        (G - sum_f' r_f') + eta r_f, traced to the face; the volume integral keeps G."""
+        geo, b = self.geo, self.b
+        K, n = self.K, self.n
+        J = geo.J.unsqueeze(1).unsqueeze(1)  # [K,1,1,n,n,n]
+        r = []
+        for s in range(6):
+            l, sgn = s // 2, (-1 if s % 2 == 0 else 1)
+            n_own = sgn * prolong(geo.Ja[:, l], b.l_side(sgn), l)  # [K,3 (d),q,p]
+            jump = Qf[:, s] - Wf[:, s].unsqueeze(2) * n_own.unsqueeze(1)  # [K,5,3,q,p]
+            rs = torch.stack([spread(jump[:, :, d], b.lhat_side(sgn), l) for d in range(3)], dim=1)  # [K,3,5,...]
+            r.append(rs / J)
+        broken = G - sum(r)
+        out = []
+        for s in range(6):
+            l, sgn = s // 2, (-1 if s % 2 == 0 else 1)
+            face = prolong((broken + self.p.eta_br2 * r[s]).flatten(1, 2), b.l_side(sgn), l)
+            out.append(face)
+        return torch.stack(out, dim=1)  # [K,6,15,q,p]
 
     def _split_form(self, U, Uv, Wv, Gv, Ff):
         """Split-form volume and surface terms (Sec. 3.3, Eq. semiDiscreteSplit) on
