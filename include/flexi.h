@@ -79,6 +79,12 @@ enum { FLEXI_SPLIT_STANDARD = 0, FLEXI_SPLIT_KEP = 1, FLEXI_SPLIT_EC = 2 };
  * OUTFLOW: the inner state (extrapolation, supersonic outflow);
  * SLIP_WALL: the inner state with its normal velocity reversed (inviscid wall). */
 enum { FLEXI_BC_EXACT = 0, FLEXI_BC_OUTFLOW = 1, FLEXI_BC_SLIP_WALL = 2 };
+/* Lifting (Sec. 3.2; Bassi & Rebay): BR1 is Eq. discreteGradient, its gradient used in the
+ * volume integral and, averaged, in the viscous face flux.  BR2 keeps that volume gradient,
+ * but the viscous face flux takes on each side the broken gradient (the BR1 gradient minus
+ * the lifting r_f = (1/J) l_hat(+-1) (U* - U_e) n s_hat of every face) plus eta_br2 times
+ * the face's own lifting (FP64 / FP32, standard volume integral; no adjoint). */
+enum { FLEXI_LIFTING_BR1 = 0, FLEXI_LIFTING_BR2 = 1 };
 /* Exact states for exact-state boundary sides (and the manufactured source term). */
 enum { FLEXI_EXACT_TGV = 0, FLEXI_EXACT_FREESTREAM = 1, FLEXI_EXACT_MANUFACTURED = 2 };
 
@@ -96,7 +102,8 @@ typedef struct {
   int adjoint;          /* 1: also allocate the discrete adjoint's scratch (volume gradients
                            and face adjoints, about 37 words per DOF); 0: adjoint calls
                            return FLEXI_EUNSUPPORTED */
-  int reserved;         /* 0 */
+  int lifting;          /* FLEXI_LIFTING_* */
+  double eta_br2;       /* BR2 penalty factor (>= 0), used with FLEXI_LIFTING_BR2 */
 } flexi_params;
 
 /* Geometry and connectivity (Sec. 3.1 mapping and curl-form metrics, Eq.

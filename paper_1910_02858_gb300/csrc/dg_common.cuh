@@ -35,7 +35,8 @@ template <typename real>
 struct Phys {
   real gamma, gm1, inv_gm1, mu, lam_th;  // lam_th = mu gamma / ((gamma-1) Pr)
   real Ma;
-  int riemann;  // 0 Roe, 1 HLLC, 2 Roe with smoothed |lambda|
+  real eta_br2;  // BR2 penalty on a face's own lifting
+  int riemann;  // 0 Roe, 1 HLLC, 2 Roe with smoothed |lambda|, 3 Rusanov, 4 entropy conservative
   int bc_exact;
 };
 

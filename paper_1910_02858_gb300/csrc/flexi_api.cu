@@ -235,6 +235,7 @@ void fill_phys(Phys<real>& ph, const flexi_params& p) {
   ph.mu = (real)p.mu;
   ph.lam_th = (real)(p.mu * p.gamma / ((p.gamma - 1.0) * p.Pr));
   ph.Ma = (real)p.Ma;
+  ph.eta_br2 = (real)p.eta_br2;
   ph.riemann = p.riemann;
   ph.bc_exact = p.bc_exact;
 }
@@ -548,6 +549,7 @@ flexi_status mesh_init_impl(flexi_ctx* c, const flexi_params* p, int K, const do
   c->m.sweep_mode = p->precision == FLEXI_FP32_TF32 ? 1 : (p->precision == FLEXI_FP32_BF16 ? 2 : 0);
   c->m.lgl = p->node_type == FLEXI_NODES_LOBATTO ? 1 : 0;
   c->m.split = p->split_form;
+  c->m.br2 = p->lifting == FLEXI_LIFTING_BR2 ? 1 : 0;
   const size_t rs = c->rs;
   if (c->fp64) {
     c->m.Ja = c->Ja64; c->m.sJ = c->sJ64; c->m.fgeo = c->fgeo64;
@@ -711,6 +713,11 @@ flexi_status flexi_mesh_init_mortar(flexi_ctx** out, const flexi_params* p, int 
   if (p->precision < FLEXI_FP64 || p->precision > FLEXI_FP32_BF16) return FLEXI_EINVAL;
   if (p->split_form < FLEXI_SPLIT_STANDARD || p->split_form > FLEXI_SPLIT_EC) return FLEXI_EINVAL;
   if (p->adjoint != 0 && p->adjoint != 1) return FLEXI_EINVAL;
+  if (p->lifting != FLEXI_LIFTING_BR1 && p->lifting != FLEXI_LIFTING_BR2) return FLEXI_EINVAL;
+  if (p->lifting == FLEXI_LIFTING_BR2 && !(p->eta_br2 >= 0.0)) return FLEXI_EINVAL;
+  if (p->lifting == FLEXI_LIFTING_BR2 &&
+      (p->split_form != FLEXI_SPLIT_STANDARD || (p->precision != FLEXI_FP64 && p->precision != FLEXI_FP32)))
+    return FLEXI_EUNSUPPORTED;
   if (p->split_form != FLEXI_SPLIT_STANDARD &&
       (p->node_type != FLEXI_NODES_LOBATTO || (p->precision != FLEXI_FP64 && p->precision != FLEXI_FP32)))
     return FLEXI_EUNSUPPORTED;
@@ -763,7 +770,7 @@ flexi_status flexi_rk_step_stages(flexi_ctx* c, void* U, void* dU, double t, dou
 }
 
 static bool adjoint_supported(const flexi_ctx* c) {
-  return c->p.adjoint && c->nBC == 0 && c->nMortar == 0 &&
+  return c->p.adjoint && c->p.lifting == FLEXI_LIFTING_BR1 && c->nBC == 0 && c->nMortar == 0 &&
          (c->p.riemann == FLEXI_RIEMANN_ROE || c->p.riemann == FLEXI_RIEMANN_ROE_SMOOTH) && !c->p.source &&
          c->p.split_form == FLEXI_SPLIT_STANDARD;
 }

@@ -274,7 +274,7 @@ __global__ void k_bc(const double* __restrict__ xbc, const int* __restrict__ bcK
 // SPLIT (Gauss-Lobatto, SW = 0 only): the split-form volume integral of Sec. 3.3 with the
 // kinetic-energy-preserving flux (1) or the entropy-conservative flux (2)
 // (Eq. semiDiscreteSplit) with the kinetic-energy-preserving two-point flux.
-template <typename real, int n, int SW, bool LGL, int SPLIT = 0>
+template <typename real, int n, int SW, bool LGL, int SPLIT = 0, bool BR2 = false>
 __global__ void __launch_bounds__(Cfg<n>::T) k_lift_vol(
     const real* __restrict__ U, const real* __restrict__ Ja, const real* __restrict__ sJ,
     const real* __restrict__ Wf, const real* __restrict__ fgeo, const int* __restrict__ elemSide,
@@ -288,9 +288,12 @@ __global__ void __launch_bounds__(Cfg<n>::T) k_lift_vol(
   real* sOut = sbuf + NE * 15 * n3p;               // [NE][5][n3p]  sweep results (not for FP64)
   real* sQ = sOut + nout;                          // [NE][6][15][n2]  (v*3+d)
   real* sO = sQ + NE * 6 * 15 * n2;  // SPLIT, FP64: [NE][3][5][n3p] two-point sums per direction
-  real* sOp = sO + ((SPLIT && sizeof(real) == 8) ? NE * 3 * NV * n3p : 0);  // DhatT, lm, lp, lhm, lhp (+ DT)
+  real* sJm = sO + ((SPLIT && sizeof(real) == 8) ? NE * 3 * NV * n3p : 0);  // BR2: [NE][6][15][n2] jumps
+  real* sSJ = sJm + (BR2 ? NE * 6 * 15 * n2 : 0);                          // BR2: [NE][n3p] 1/J
+  real* sOp = sSJ + (BR2 ? NE * n3p : 0);  // DhatT, lm, lp, lhm, lhp (+ DT)
   int* sES = reinterpret_cast<int*>(sOp + n2 + 4 * n + (SPLIT ? n2 : 0));
   static_assert(!SPLIT || (LGL && SW == 0), "the split form is built on Gauss-Lobatto nodes with CUDA-core sweeps");
+  static_assert(!BR2 || (SW == 0 && !SPLIT), "BR2 face gradients are built for the standard form, CUDA-core sweeps");
 
   const int tid = threadIdx.x;
   const int el = tid / n3, node = tid - el * n3;
@@ -333,24 +336,31 @@ __global__ void __launch_bounds__(Cfg<n>::T) k_lift_vol(
     const int es = sES[el2 * 6 + s];
     const int side = es_side(es);
     const int mpq = orient_pq(es_orient(es), n - 1, pq % n, pq / n);
-    if (side >= bigBase) {
-      const real* qb = QB + ((size_t)(side - bigBase) * 15) * n2 + mpq;
-      real* Q = sQ + ((el2 * 6 + s) * 15) * n2 + pq;
-#pragma unroll
-      for (int c = 0; c < 15; ++c) Q[c * n2] = qb[c * n2];
-      continue;
-    }
     const real* w0 = Wf + ((size_t)side * NV) * n2 + mpq;
     const real* w1 = Wf + ((size_t)(S + side) * NV) * n2 + mpq;
     const real* g = fgeo + ((size_t)side * 4) * n2 + mpq;
     const real sc = es_slave(es) ? -g[3 * n2] : g[3 * n2];
     const real nd[3] = {g[0] * sc, g[n2] * sc, g[2 * n2] * sc};
     real* Q = sQ + ((el2 * 6 + s) * 15) * n2 + pq;
+    if (side >= bigBase) {
+      const real* qb = QB + ((size_t)(side - bigBase) * 15) * n2 + mpq;
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      const real ws = real(0.5) * (w0[v * n2] + w1[v * n2]);
+      for (int c = 0; c < 15; ++c) Q[c * n2] = qb[c * n2];
+    } else {
 #pragma unroll
-      for (int d = 0; d < 3; ++d) Q[(v * 3 + d) * n2] = ws * nd[d];
+      for (int v = 0; v < NV; ++v) {
+        const real ws = real(0.5) * (w0[v * n2] + w1[v * n2]);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) Q[(v * 3 + d) * n2] = ws * nd[d];
+      }
+    }
+    if constexpr (BR2) {  // jump (U* - U_e) n s_hat with the element's own face state
+      const real* wo = es_slave(es) ? w1 : w0;
+      real* Jm = sJm + ((el2 * 6 + s) * 15) * n2 + pq;
+#pragma unroll
+      for (int v = 0; v < NV; ++v)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) Jm[(v * 3 + d) * n2] = Q[(v * 3 + d) * n2] - wo[v * n2] * nd[d];
     }
   }
 
@@ -409,15 +419,57 @@ __global__ void __launch_bounds__(Cfg<n>::T) k_lift_vol(
     for (int v = 0; v < NV; ++v) G[d * NV + v] = acc[v] * sj;
   }
 
-  // a4: gradients to the faces
+  // a4: gradients to the faces (BR2: the broken gradient, G minus every face's
+  // lifting r_f = (1/J) l_hat(+-1) (U* - U_e) n s_hat, plus eta r_f on face f below)
   __syncthreads();
+  if constexpr (BR2) {
+    const real* Je = sJm + el * 6 * 15 * n2;
+    const real c0 = lhm[i], c1 = lhp[i], c2 = lhm[j], c3 = lhp[j], c4 = lhm[k], c5 = lhp[k];
 #pragma unroll
-  for (int c = 0; c < 15; ++c) myb[c * n3p + pn] = G[c];
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const int o = (v * 3 + d) * n2;
+        real rr;
+        if constexpr (LGL) {
+          rr = real(0);
+          if (i == 0) rr += lhm[0] * Je[0 * 15 * n2 + o + pq0];
+          if (i == n - 1) rr += lhp[n - 1] * Je[1 * 15 * n2 + o + pq0];
+          if (j == 0) rr += lhm[0] * Je[2 * 15 * n2 + o + pq1];
+          if (j == n - 1) rr += lhp[n - 1] * Je[3 * 15 * n2 + o + pq1];
+          if (k == 0) rr += lhm[0] * Je[4 * 15 * n2 + o + pq2];
+          if (k == n - 1) rr += lhp[n - 1] * Je[5 * 15 * n2 + o + pq2];
+        } else {
+          rr = c0 * Je[0 * 15 * n2 + o + pq0] + c1 * Je[1 * 15 * n2 + o + pq0] + c2 * Je[2 * 15 * n2 + o + pq1] +
+               c3 * Je[3 * 15 * n2 + o + pq1] + c4 * Je[4 * 15 * n2 + o + pq2] + c5 * Je[5 * 15 * n2 + o + pq2];
+        }
+        myb[(d * NV + v) * n3p + pn] = G[d * NV + v] - sj * rr;
+      }
+    sSJ[el * n3p + pn] = sj;
+  } else {
+#pragma unroll
+    for (int c = 0; c < 15; ++c) myb[c * n3p + pn] = G[c];
+  }
   if (Gvol != nullptr && valid) {
 #pragma unroll
     for (int c = 0; c < 15; ++c) Gvol[((size_t)e * 15 + c) * n3 + node] = G[c];
   }
   __syncthreads();
+  // BR2: eta times the trace of face s's own lifting at face node (p, q), component c = d*5 + v
+  auto br2_own = [&](int el2, int s, int c, int p, int q) -> real {
+    const int l = s >> 1;
+    const real* sjl = sSJ + el2 * n3p;
+    real kap = real(0);
+    if (LGL) {
+      kap = ((s & 1) ? lhp[n - 1] : lhm[0]) * sjl[pvol_index<n>(l, (s & 1) ? n - 1 : 0, p, q)];
+    } else {
+#pragma unroll
+      for (int a = 0; a < n; ++a)
+        kap += ((s & 1) ? ops.lp[a] * lhp[a] : ops.lm[a] * lhm[a]) * sjl[pvol_index<n>(l, a, p, q)];
+    }
+    const int v = c % NV, d = c / NV;
+    return ph.eta_br2 * kap * sJm[((el2 * 6 + s) * 15 + v * 3 + d) * n2 + p + n * q];
+  };
   if constexpr (sizeof(real) == 8) {
     // FP64: one thread per (face node, component), more warps on the FP64 pipe
     for (int it = tid; it < NE * 6 * 15 * n2; it += T) {
@@ -436,6 +488,7 @@ __global__ void __launch_bounds__(Cfg<n>::T) k_lift_vol(
 #pragma unroll
         for (int a = 0; a < n; ++a) val += ((s & 1) ? ops.lp[a] : ops.lm[a]) * b[pvol_index<n>(l, a, p, q)];
       }
+      if constexpr (BR2) val += br2_own(el2, s, c, p, q);
       const int es = sES[el2 * 6 + s];
       const int mpq = orient_pq(es_orient(es), n - 1, p, q);
       Gf[((size_t)(es_slave(es) * S + es_side(es)) * 15 + c) * n2 + mpq] = val;
@@ -466,6 +519,10 @@ __global__ void __launch_bounds__(Cfg<n>::T) k_lift_vol(
           gm += ops.lm[a] * x;
           gp += ops.lp[a] * x;
         }
+      }
+      if constexpr (BR2) {
+        gm += br2_own(el2, 2 * l, c, p, q);
+        gp += br2_own(el2, 2 * l + 1, c, p, q);
       }
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
@@ -716,13 +773,14 @@ __global__ void __launch_bounds__(Cfg<n>::T) k_lift_vol(
   }
 }
 
-template <typename real, int n, int SW, int SPLIT = 0>
+template <typename real, int n, int SW, int SPLIT = 0, bool BR2 = false>
 constexpr size_t lift_vol_smem() {
   using C = Cfg<n>;
   // the FP64 form sweeps per node and needs no result buffer
   constexpr int out = (sizeof(real) == 8 && SW == 0) ? 0 : C::NE * NV * C::n3p;
   return sizeof(real) * (C::NE * 15 * C::n3p + out + C::NE * 6 * 15 * C::n2 + C::n2 + 4 * n +
-                         (SPLIT ? C::n2 : 0) + ((SPLIT && sizeof(real) == 8) ? C::NE * 3 * NV * C::n3p : 0)) +
+                         (SPLIT ? C::n2 : 0) + ((SPLIT && sizeof(real) == 8) ? C::NE * 3 * NV * C::n3p : 0) +
+                         (BR2 ? C::NE * 6 * 15 * C::n2 + C::NE * C::n3p : 0)) +
          sizeof(int) * C::NE * 6;
 }
 
@@ -916,20 +974,20 @@ cudaError_t launch_bc(const DevMesh& m, double t, const Phys<real>& ph, cudaStre
   return cudaGetLastError();
 }
 
-template <typename real, int n, int SW, bool LGL = false, int SPLIT = 0>
+template <typename real, int n, int SW, bool LGL = false, int SPLIT = 0, bool BR2 = false>
 static cudaError_t lift_vol_n(const DevMesh& m, const real* U, const Ops<real>& ops, const Phys<real>& ph,
                               int store_grad, cudaStream_t st) {
   using C = Cfg<n>;
-  constexpr size_t smem = lift_vol_smem<real, n, SW, SPLIT>();
+  constexpr size_t smem = lift_vol_smem<real, n, SW, SPLIT, BR2>();
   static bool attr = false;
   if (!attr) {
-    cudaError_t err = cudaFuncSetAttribute(k_lift_vol<real, n, SW, LGL, SPLIT>,
+    cudaError_t err = cudaFuncSetAttribute(k_lift_vol<real, n, SW, LGL, SPLIT, BR2>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     attr = true;
   }
   const int grid = (m.K + C::NE - 1) / C::NE;
-  k_lift_vol<real, n, SW, LGL, SPLIT><<<grid, C::T, smem, st>>>(U, (const real*)m.Ja, (const real*)m.sJ,
+  k_lift_vol<real, n, SW, LGL, SPLIT, BR2><<<grid, C::T, smem, st>>>(U, (const real*)m.Ja, (const real*)m.sJ,
                                                          (const real*)m.Wf, (const real*)m.fgeo, m.elemSide,
                                                          (real*)m.Gf, (real*)m.Utv,
                                                          store_grad ? (real*)m.Gvol : nullptr, m.K, m.S,
@@ -947,6 +1005,12 @@ cudaError_t launch_lift_vol(const DevMesh& m, const real* U, const Ops<real>& op
     } else if (m.sweep_mode == 2) {
       FLEXI_DISPATCH_N(m.n, return lift_vol_n<real, NN, 2>(m, U, ops, ph, store_grad, st));
     }
+  }
+  if (m.br2) {
+    if (m.lgl) {
+      FLEXI_DISPATCH_N(m.n, return lift_vol_n<real, NN, 0, true, 0, true>(m, U, ops, ph, store_grad, st));
+    }
+    FLEXI_DISPATCH_N(m.n, return lift_vol_n<real, NN, 0, false, 0, true>(m, U, ops, ph, store_grad, st));
   }
   if (m.lgl && m.split == 1) {
     FLEXI_DISPATCH_N(m.n, return lift_vol_n<real, NN, 0, true, 1>(m, U, ops, ph, store_grad, st));

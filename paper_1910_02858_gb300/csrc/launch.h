@@ -14,6 +14,7 @@ struct DevMesh {
   int sweep_mode = 0;          // 0 CUDA-core line sweeps, 1 TF32 and 2 BF16 3-term split mma
   int lgl = 0;                 // 1: Gauss-Lobatto nodes (face terms only at face nodes)
   int split = 0;               // split-form volume integral: 1 kinetic-energy-preserving, 2 entropy-conservative flux
+  int br2 = 0;                 // 1: BR2 face gradients for the viscous numerical flux
   const void* Ja = nullptr;    // [K][9][n^3]   Ja^l_d at index l*3+d
   const void* sJ = nullptr;    // [K][n^3]      1/J
   const void* fgeo = nullptr;  // [S][4][n^2]   n_hat (3), s_hat

@@ -22,6 +22,7 @@ EXACT_TGV, EXACT_FREESTREAM, EXACT_MANUFACTURED = 0, 1, 2
 SPLIT_STANDARD, SPLIT_KEP, SPLIT_EC = 0, 1, 2
 CONN_MORTAR = -(1 << 30)
 BC_EXACT, BC_OUTFLOW, BC_SLIP_WALL = 0, 1, 2
+LIFTING_BR1, LIFTING_BR2 = 0, 1
 Q_K, Q_N, Q_NSIDES, Q_NBCSIDES, Q_DOF, Q_BYTES_PER_STAGE, Q_FLOPS_PER_STAGE, Q_STATUS, Q_DEVICE_BYTES, Q_PRECISION = range(10)
 KERNEL_CLASSES = ["lift_vol", "face", "surf_rk", "prolong", "bc", "adjoint", "reduce", "other"]
 
@@ -37,7 +38,7 @@ class flexi_params(ctypes.Structure):
                 ("precision", ctypes.c_int), ("bc_exact", ctypes.c_int), ("source", ctypes.c_int),
                 ("split_form", ctypes.c_int), ("gamma", ctypes.c_double), ("Pr", ctypes.c_double),
                 ("mu", ctypes.c_double), ("Ma", ctypes.c_double), ("adjoint", ctypes.c_int),
-                ("reserved2", ctypes.c_int)]
+                ("lifting", ctypes.c_int), ("eta_br2", ctypes.c_double)]
 
 
 class FlexiError(RuntimeError):

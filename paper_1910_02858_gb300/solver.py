@@ -23,6 +23,8 @@ class SolverConfig:
     source: bool = False
     split_form: int = F.SPLIT_STANDARD
     adjoint: bool = False  # allocate the discrete adjoint's scratch
+    lifting: int = F.LIFTING_BR1
+    eta_br2: float = 2.0
     gamma: float = 1.4
     Pr: float = 0.72
     mu: float = 1.0 / 1600.0
@@ -32,7 +34,7 @@ class SolverConfig:
         return F.flexi_params(N=self.N, Ngeo=self.Ngeo, node_type=self.node_type, riemann=self.riemann,
                               precision=self.precision, bc_exact=self.bc_exact, source=int(self.source),
                               split_form=self.split_form, gamma=self.gamma, Pr=self.Pr, mu=self.mu, Ma=self.Ma,
-                              adjoint=int(self.adjoint))
+                              adjoint=int(self.adjoint), lifting=self.lifting, eta_br2=self.eta_br2)
 
 
 class Solver:

@@ -51,7 +51,8 @@ def _oracle(cfg_kw, mesh):
                         smooth_roe=cfg_kw.get("riemann", 0) == 2, mu=cfg_kw.get("mu", 1 / 1600.0),
                         Ma=cfg_kw.get("Ma", 0.1), bc_exact=bc, source=cfg_kw.get("source", False),
                         gamma=cfg_kw.get("gamma", 1.4), Pr=cfg_kw.get("Pr", 0.72),
-                        split={0: "", 1: "pirozzoli", 2: "chandrashekar"}[cfg_kw.get("split_form", 0)]),
+                        split={0: "", 1: "pirozzoli", 2: "chandrashekar"}[cfg_kw.get("split_form", 0)],
+                        lifting="br2" if cfg_kw.get("lifting", 0) == 1 else "br1", eta_br2=cfg_kw.get("eta_br2", 2.0)),
                  mesh.coords, mesh.conn)
 
 
