@@ -83,7 +83,67 @@ __device__ __forceinline__ void line_sweep3(const real* __restrict__ buf, real* 
   }
 }
 
-// Per-node form of the same three sweeps (used by the FP64 form, which is bound
+// The FP32 CUDA-core lifting sweeps either 5 fields per (gradient component,
+// direction) (line_sweep3, nine sweeps) or 15 fields per direction (lift_sweep,
+// three sweeps); the 15-field form is taken where it fills the CTA's threads
+// better: 3 * passes(5 fields) > passes(15 fields), with passes = ceil(lines / T).
+// n = 8: 320 of 512 threads busy in one pass against 960 tasks in two; n = 5, 6, 7
+// fill equally (or worse) and keep the 5-field sweeps.
+template <int n>
+constexpr bool lift15_fills_better() {
+  using C = Cfg<n>;
+  constexpr int L5 = C::NE * NV * C::n2, T = C::T;
+  return 3 * ((L5 + T - 1) / T) > (3 * L5 + T - 1) / T;
+}
+
+// One line of lift_sweep (task it = (element, field d*5+v, line)).
+template <typename real, int n, bool LGL, int l>
+__device__ __forceinline__ void lift_line(const real* __restrict__ buf, real* __restrict__ out,
+                                          const real* __restrict__ Q, const Ops<real>& ops, int it) {
+  using C = Cfg<n>;
+  constexpr int n2 = C::n2, n3p = C::n3p, P = C::P;
+  constexpr int stride = l == 0 ? 1 : (l == 1 ? P : P * n);
+  const int el = it / (15 * n2);
+  const int r = it - el * 15 * n2;
+  const int c = r / n2, line = r - c * n2;
+  const int d = c / NV, v = c - d * NV;
+  const int a0 = line % n, a1 = line / n;  // free indices in increasing direction order
+  const int base = l == 0 ? P * line : (l == 1 ? a0 + P * n * a1 : a0 + P * a1);
+  const real* src = buf + (el * 15 + c) * n3p + base;
+  real x[n];
+#pragma unroll
+  for (int a = 0; a < n; ++a) x[a] = src[a * stride];
+  const real qm = Q[((el * 6 + 2 * l) * 15 + v * 3 + d) * n2 + line];
+  const real qp = Q[((el * 6 + 2 * l + 1) * 15 + v * 3 + d) * n2 + line];
+  real* dst = out + (el * 15 + c) * n3p + base;
+#pragma unroll
+  for (int ii = 0; ii < n; ++ii) {
+    real y = LGL ? (ii == 0 ? ops.lhm[0] * qm : (ii == n - 1 ? ops.lhp[n - 1] * qp : real(0)))
+                 : ops.lhm[ii] * qm + ops.lhp[ii] * qp;
+#pragma unroll
+    for (int a = 0; a < n; ++a) y += ops.DhatT[a * n + ii] * x[a];
+    dst[ii * stride] = (l == 0) ? y : dst[ii * stride] + y;
+  }
+}
+
+// Lifting sweep along one reference direction l for all three gradient components
+// at once (FP32 CUDA-core form): buf[el][d*5+v][node] = Ja^l_d W_v is swept with
+// D_hat along l into out[el][d*5+v][node] (written for l = 0, accumulated after),
+// the face terms l_hat_i(-1) Q[-face] + l_hat_i(+1) Q[+face] of direction l folded
+// in.  15 fields x n^2 lines per element keep every thread of the CTA busy, and
+// the lifting needs three sweeps instead of nine.  Block-wide; ends synced.
+template <typename real, int n, bool LGL, int l>
+__device__ __forceinline__ void lift_sweep(const real* __restrict__ buf, real* __restrict__ out,
+                                           const real* __restrict__ Q, const Ops<real>& ops, int tid) {
+  using C = Cfg<n>;
+  constexpr int L = C::NE * 15 * C::n2, T = C::T;
+#pragma unroll
+  for (int k = 0; k < (L + T - 1) / T; ++k)  // compile-time trip count (a runtime loop spills)
+    if (tid + k * T < L) lift_line<real, n, LGL, l>(buf, out, Q, ops, tid + k * T);
+  __syncthreads();
+}
+
+// Per-node form of line_sweep3's three sweeps (used by the FP64 form, which is bound
 // by the FP64 pipe and short of registers for whole lines): the thread of node
 // (i,j,k) accumulates sum_a Dhat[i][a] f0(a,j,k) + Dhat[j][a] f1(i,a,k) +
 // Dhat[k][a] f2(i,j,a) for the 5 variables, reading the padded staged fields.
@@ -275,7 +335,7 @@ __global__ void k_bc(const double* __restrict__ xbc, const int* __restrict__ bcK
 // kinetic-energy-preserving flux (1) or the entropy-conservative flux (2)
 // (Eq. semiDiscreteSplit) with the kinetic-energy-preserving two-point flux.
 template <typename real, int n, int SW, bool LGL, int SPLIT = 0, bool BR2 = false>
-__global__ void __launch_bounds__(Cfg<n>::T) k_lift_vol(
+__global__ void __launch_bounds__(Cfg<n>::T, (sizeof(real) == 4 && SW == 0 && Cfg<n>::T == 512) ? 2 : 1) k_lift_vol(
     const real* __restrict__ U, const real* __restrict__ Ja, const real* __restrict__ sJ,
     const real* __restrict__ Wf, const real* __restrict__ fgeo, const int* __restrict__ elemSide,
     real* __restrict__ Gf, real* __restrict__ Utv, real* __restrict__ Gvol, int K, int S, int bigBase,
@@ -284,8 +344,10 @@ __global__ void __launch_bounds__(Cfg<n>::T) k_lift_vol(
   constexpr int n2 = C::n2, n3 = C::n3, NE = C::NE, T = C::T, n3p = C::n3p;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   real* sbuf = reinterpret_cast<real*>(smem_raw);  // [NE][15][n3p] staged fields (padded lines)
-  constexpr int nout = (sizeof(real) == 8 && SW == 0) ? 0 : NE * NV * n3p;
-  real* sOut = sbuf + NE * 15 * n3p;               // [NE][5][n3p]  sweep results (not for FP64)
+  // FP32 CUDA-core form (not BR2): the lifting may sweep all three gradient components per direction
+  constexpr bool kLift15 = SW == 0 && sizeof(real) == 4 && !BR2 && lift15_fills_better<n>();
+  constexpr int nout = (sizeof(real) == 8 && SW == 0) ? 0 : NE * (kLift15 ? 15 : NV) * n3p;
+  real* sOut = sbuf + NE * 15 * n3p;  // [NE][5 or 15][n3p]  sweep results (not for FP64)
   real* sQ = sOut + nout;                          // [NE][6][15][n2]  (v*3+d)
   real* sO = sQ + NE * 6 * 15 * n2;  // SPLIT, FP64: [NE][3][5][n3p] two-point sums per direction
   real* sJm = sO + ((SPLIT && sizeof(real) == 8) ? NE * 3 * NV * n3p : 0);  // BR2: [NE][6][15][n2] jumps
@@ -370,8 +432,25 @@ __global__ void __launch_bounds__(Cfg<n>::T) k_lift_vol(
   const real* lhp = sOp + n2 + 3 * n;
   const real* Qe = sQ + el * 6 * 15 * n2;
   const int pq0 = j + n * k, pq1 = i + n * k, pq2 = i + n * j;
+  if constexpr (kLift15) {
 #pragma unroll
-  for (int d = 0; d < 3; ++d) {
+    for (int l = 0; l < 3; ++l) {  // the previous sweep ended synced: sbuf is free
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const real a = jac[l * 3 + d];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) myb[(d * NV + v) * n3p + pn] = a * W[v];
+      }
+      __syncthreads();
+      if (l == 0) lift_sweep<real, n, LGL, 0>(sbuf, sOut, sQ, ops, tid);
+      if (l == 1) lift_sweep<real, n, LGL, 1>(sbuf, sOut, sQ, ops, tid);
+      if (l == 2) lift_sweep<real, n, LGL, 2>(sbuf, sOut, sQ, ops, tid);
+    }
+#pragma unroll
+    for (int c = 0; c < 15; ++c) G[c] = sOut[(el * 15 + c) * n3p + pn] * sj;
+  }
+#pragma unroll
+  for (int d = 0; d < (kLift15 ? 0 : 3); ++d) {
     __syncthreads();
 #pragma unroll
     for (int l = 0; l < 3; ++l) {
@@ -776,8 +855,11 @@ __global__ void __launch_bounds__(Cfg<n>::T) k_lift_vol(
 template <typename real, int n, int SW, int SPLIT = 0, bool BR2 = false>
 constexpr size_t lift_vol_smem() {
   using C = Cfg<n>;
-  // the FP64 form sweeps per node and needs no result buffer
-  constexpr int out = (sizeof(real) == 8 && SW == 0) ? 0 : C::NE * NV * C::n3p;
+  // the FP64 form sweeps per node and needs no result buffer; the FP32 CUDA-core
+  // lifting (not BR2) may sweep 15 fields at once
+  constexpr int out = (sizeof(real) == 8 && SW == 0)
+                          ? 0
+                          : C::NE * ((SW == 0 && !BR2 && lift15_fills_better<n>()) ? 15 : NV) * C::n3p;
   return sizeof(real) * (C::NE * 15 * C::n3p + out + C::NE * 6 * 15 * C::n2 + C::n2 + 4 * n +
                          (SPLIT ? C::n2 : 0) + ((SPLIT && sizeof(real) == 8) ? C::NE * 3 * NV * C::n3p : 0) +
                          (BR2 ? C::NE * 6 * 15 * C::n2 + C::NE * C::n3p : 0)) +
