@@ -176,12 +176,15 @@ flexi_status flexi_rk_step_stages(flexi_ctx *ctx, void *U, void *dU, double t, d
                                   void *stream);
 
 /* Discrete adjoint of one flexi_rk_step (reverse of the stage loop):
- *   for k = 5..1: lam_dU += B_k lamU; lamU += dt (dL/dU(U_{k-1}))^T lam_dU;
+ *   for k = 5..1: lam_dU += B_k lamU; lamU += dt (dL/dU(U_{k-1}, t + c_k dt))^T lam_dU;
  *                 lam_dU = A_k lam_dU.
- * U_stages: device [5][K][5][n^3] as written by flexi_rk_step_stages;
- * lamU, lam_dU: device, updated in place.  Requires flexi_params.adjoint = 1,
- * FLEXI_FP64 or FLEXI_FP32 and a Roe-type flux (ROE or ROE_SMOOTH); periodic
- * meshes without source term and with the standard volume integral only
+ * U_stages: device [5][K][5][n^3] as written by flexi_rk_step_stages; t: the
+ * step's start time (exact-state boundaries are evaluated at the stage times of
+ * the forward step).  lamU, lam_dU: device, updated in place.  Requires
+ * flexi_params.adjoint = 1, FLEXI_FP64 or FLEXI_FP32, a Roe-type flux (ROE or
+ * ROE_SMOOTH), BR1 lifting and the standard volume integral; periodic meshes and
+ * meshes with boundaries of every kind (the outer state's dependence on the
+ * inner one is transposed; a source term does not depend on U); no mortars
  * (FLEXI_EUNSUPPORTED otherwise). */
 flexi_status flexi_adjoint_step(flexi_ctx *ctx, const void *U_stages, void *lamU, void *lam_dU, double t,
                                 double dt, void *stream);

@@ -589,24 +589,25 @@ flexi_status mesh_init_impl(flexi_ctx* c, const flexi_params* p, int K, const do
 
 template <typename real>
 flexi_status do_rhs_adjoint(flexi_ctx* c, const real* U, const real* lam, real* out, real scale, int accumulate,
-                            cudaStream_t st) {
+                            double t, cudaStream_t st) {
   Prof pr(c, KC_ADJ, st);
   CK(launch_rhs_adjoint<real>(c->m, U, lam, out, scale, accumulate, ops_of<real>(c), ph_of<real>(c), c->adj_scratch,
-                              st));
+                              t, st));
   return FLEXI_OK;
 }
 
 // reverse of one LSERK4(5) step (Williamson 2N form):
-//   for k = 5..1: lam_dU += B_k lamU; lamU += dt (dL/dU(U_{k-1}))^T lam_dU; lam_dU = A_k lam_dU
+//   for k = 5..1: lam_dU += B_k lamU; lamU += dt (dL/dU(U_{k-1}, t + c_k dt))^T lam_dU; lam_dU = A_k lam_dU
 template <typename real>
-flexi_status do_adjoint_step(flexi_ctx* c, const real* stages, real* lamU, real* lam_dU, double dt, cudaStream_t st) {
+flexi_status do_adjoint_step(flexi_ctx* c, const real* stages, real* lamU, real* lam_dU, double t, double dt,
+                             cudaStream_t st) {
   const size_t nU = (size_t)c->K * NV * c->n3;
   for (int k = 4; k >= 0; --k) {
     {
       Prof pr(c, KC_OTHER, st);
       CK(launch_axpby<real>(lam_dU, lamU, real(1), (real)RK_B[k], nU, st));
     }
-    flexi_status s = do_rhs_adjoint<real>(c, stages + k * nU, lam_dU, lamU, (real)dt, 1, st);
+    flexi_status s = do_rhs_adjoint<real>(c, stages + k * nU, lam_dU, lamU, (real)dt, 1, t + RK_C[k] * dt, st);
     if (s != FLEXI_OK) return s;
     Prof pr(c, KC_OTHER, st);
     CK(launch_axpby<real>(lam_dU, nullptr, (real)RK_A[k], real(0), nU, st));
@@ -770,8 +771,8 @@ flexi_status flexi_rk_step_stages(flexi_ctx* c, void* U, void* dU, double t, dou
 }
 
 static bool adjoint_supported(const flexi_ctx* c) {
-  return c->p.adjoint && c->p.lifting == FLEXI_LIFTING_BR1 && c->nBC == 0 && c->nMortar == 0 &&
-         (c->p.riemann == FLEXI_RIEMANN_ROE || c->p.riemann == FLEXI_RIEMANN_ROE_SMOOTH) && !c->p.source &&
+  return c->p.adjoint && c->p.lifting == FLEXI_LIFTING_BR1 && c->nMortar == 0 &&
+         (c->p.riemann == FLEXI_RIEMANN_ROE || c->p.riemann == FLEXI_RIEMANN_ROE_SMOOTH) &&
          c->p.split_form == FLEXI_SPLIT_STANDARD;
 }
 
@@ -779,19 +780,17 @@ flexi_status flexi_adjoint_step(flexi_ctx* c, const void* U_stages, void* lamU, 
                                 void* stream) {
   if (c == nullptr || U_stages == nullptr || lamU == nullptr || lam_dU == nullptr) return FLEXI_EINVAL;
   if (!adjoint_supported(c)) return FLEXI_EUNSUPPORTED;
-  (void)t;  // the operator is autonomous on periodic meshes without source terms
   cudaStream_t st = (cudaStream_t)stream;
-  return c->fp64 ? do_adjoint_step<double>(c, (const double*)U_stages, (double*)lamU, (double*)lam_dU, dt, st)
-                 : do_adjoint_step<float>(c, (const float*)U_stages, (float*)lamU, (float*)lam_dU, dt, st);
+  return c->fp64 ? do_adjoint_step<double>(c, (const double*)U_stages, (double*)lamU, (double*)lam_dU, t, dt, st)
+                 : do_adjoint_step<float>(c, (const float*)U_stages, (float*)lamU, (float*)lam_dU, t, dt, st);
 }
 
 flexi_status flexi_rhs_adjoint(flexi_ctx* c, const void* U, const void* lam, void* out, double t, void* stream) {
   if (c == nullptr || U == nullptr || lam == nullptr || out == nullptr) return FLEXI_EINVAL;
   if (!adjoint_supported(c)) return FLEXI_EUNSUPPORTED;
-  (void)t;
   cudaStream_t st = (cudaStream_t)stream;
-  return c->fp64 ? do_rhs_adjoint<double>(c, (const double*)U, (const double*)lam, (double*)out, 1.0, 0, st)
-                 : do_rhs_adjoint<float>(c, (const float*)U, (const float*)lam, (float*)out, 1.0f, 0, st);
+  return c->fp64 ? do_rhs_adjoint<double>(c, (const double*)U, (const double*)lam, (double*)out, 1.0, 0, t, st)
+                 : do_rhs_adjoint<float>(c, (const float*)U, (const float*)lam, (float*)out, 1.0f, 0, t, st);
 }
 
 // true when one RK step does not depend on t: no source term and no exact-state

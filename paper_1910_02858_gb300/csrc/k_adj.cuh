@@ -1,9 +1,15 @@
 // Discrete adjoint of the right-hand side: mu = (dL/dU)^T lam, by hand-written
 // reverse mode of every step of the forward operator (steps a1..a9 of k_dg.cuh),
-// for periodic meshes and the Roe flux (optionally with smoothed |lambda|).
+// for the Roe flux (optionally with smoothed |lambda|), BR1 lifting and the
+// standard volume integral, on periodic meshes and meshes with boundary sides.
+// Boundary sides: the outer state is a function of the inner one (outflow: the
+// same state; slip wall: normal velocity reversed, a reflection; exact state:
+// independent of U) and the outer gradient is the inner one, so their adjoints
+// flow back to the inner face state and gradient.  Source terms do not depend
+// on U and drop out.
 //
-// Forward recompute (k_prolong, k_lift_vol with the volume gradients stored),
-// then, in reverse order of the forward data flow:
+// Forward recompute (k_prolong, k_bc, k_lift_vol with the volume gradients
+// stored), then, in reverse order of the forward data flow:
 //   k_adj_lamface  element: lam_vol = -lam/J; its l_hat-weighted face values
 //                  (transpose of the surface integral a8/a9)
 //   k_adj_face     side: reverse of the numerical flux a5 (Roe + BR1 viscous)
@@ -12,8 +18,8 @@
 //                  VJP), a4 (prolongation^T of the face-gradient adjoints), a3
 //                  (lifting: 45 D_hat^T sweeps and the l_hat face projections),
 //                  and the primitive map of the volume states
-//   k_adj_side     side: BR1 mean (U* = (U_L + U_R)/2) and the primitive map of
-//                  the face states
+//   k_adj_side     side: BR1 mean (U* = (U_L + U_R)/2), the boundary state's
+//                  transpose and the primitive map of the face states
 //   k_adj_gather   element: prolongation^T of the face-state adjoints; out =
 //                  (accumulate ? out : 0) + scale * mu
 #pragma once
@@ -314,23 +320,26 @@ __global__ void __launch_bounds__(Cfg<n>::T) k_adj_lamface(const real* __restric
 template <typename real, int n>
 __global__ void __launch_bounds__(128) k_adj_face(const real* __restrict__ Wf, const real* __restrict__ Gf,
                                                   const real* __restrict__ fgeo, const real* __restrict__ LF,
-                                                  real* __restrict__ LWf, real* __restrict__ LGf, int S, Phys<real> ph) {
+                                                  real* __restrict__ LWf, real* __restrict__ LGf, int S, int nBC,
+                                                  Phys<real> ph) {
   constexpr int n2 = n * n;
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= S * n2) return;
   const int side = idx / n2, pq = idx - side * n2;
+  const bool bnd = side < nBC;  // boundary side: no slave element, outer gradient = inner gradient
   real WL[NV], WR[NV], GL[15], GR[15], nv[3], lf[NV];
   const real sa = fgeo[((size_t)side * 4 + 3) * n2 + pq];
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
     WL[v] = Wf[((size_t)side * NV + v) * n2 + pq];
     WR[v] = Wf[((size_t)(S + side) * NV + v) * n2 + pq];
-    lf[v] = (LF[((size_t)side * NV + v) * n2 + pq] - LF[((size_t)(S + side) * NV + v) * n2 + pq]) * sa;
+    lf[v] = (LF[((size_t)side * NV + v) * n2 + pq] - (bnd ? real(0) : LF[((size_t)(S + side) * NV + v) * n2 + pq])) *
+            sa;
   }
 #pragma unroll
   for (int c = 0; c < 15; ++c) {
     GL[c] = Gf[((size_t)side * 15 + c) * n2 + pq];
-    GR[c] = Gf[((size_t)(S + side) * 15 + c) * n2 + pq];
+    GR[c] = bnd ? GL[c] : Gf[((size_t)(S + side) * 15 + c) * n2 + pq];
   }
 #pragma unroll
   for (int d = 0; d < 3; ++d) nv[d] = fgeo[((size_t)side * 4 + d) * n2 + pq];
@@ -346,6 +355,13 @@ __global__ void __launch_bounds__(128) k_adj_face(const real* __restrict__ Wf, c
     for (int v = 0; v < NV; ++v) lF[d][v] = -real(0.5) * nv[d] * lf[v];
   visc_vjp(WL, GL, lF, ph, lWL, lGL);
   visc_vjp(WR, GR, lF, ph, lWR, lGR);
+  if (bnd) {
+#pragma unroll
+    for (int c = 0; c < 15; ++c) {
+      lGL[c] += lGR[c];
+      lGR[c] = real(0);
+    }
+  }
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
     LWf[((size_t)side * NV + v) * n2 + pq] = lWL[v];
@@ -534,14 +550,50 @@ __global__ void __launch_bounds__(Cfg<n>::T) k_adj_vol(
   }
 }
 
-// side: BR1 mean and the primitive map of the face states -> adjoint of U_face
+// side: BR1 mean and the primitive map of the face states -> adjoint of U_face.
+// Boundary sides: the adjoint of the outer state W_R = B(W_L) (flux and lifting
+// mean) is added to the inner one through B^T (exact state: B = 0; outflow:
+// B = I; slip wall: the velocity reflection I - 2 n n^T, symmetric); slot 1 is
+// cleared (no element gathers it).
 template <typename real, int n>
 __global__ void __launch_bounds__(128) k_adj_side(const real* __restrict__ Wf, const real* __restrict__ LWs,
-                                                  real* __restrict__ LWf, int S, Phys<real> ph) {
+                                                  const real* __restrict__ fgeo, const int* __restrict__ bcKind,
+                                                  real* __restrict__ LWf, int S, int nBC, Phys<real> ph) {
   constexpr int n2 = n * n;
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= S * n2) return;
   const int side = idx / n2, pq = idx - side * n2;
+  if (side < nBC) {
+    real W[NV], lW[NV], lWR[NV], lU[NV] = {0, 0, 0, 0, 0};
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const size_t g0 = ((size_t)side * NV + v) * n2 + pq, g1 = ((size_t)(S + side) * NV + v) * n2 + pq;
+      W[v] = Wf[g0];
+      lW[v] = LWf[g0] + real(0.5) * LWs[g0];
+      lWR[v] = LWf[g1] + real(0.5) * LWs[g0];
+    }
+    const int kind = bcKind[side];
+    if (kind == 1) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) lW[v] += lWR[v];
+    } else if (kind == 2) {
+      const real* g = fgeo + ((size_t)side * 4) * n2 + pq;
+      const real nx = g[0], ny = g[n2], nz = g[2 * n2];
+      const real ln = lWR[1] * nx + lWR[2] * ny + lWR[3] * nz;
+      lW[0] += lWR[0];
+      lW[1] += lWR[1] - real(2) * ln * nx;
+      lW[2] += lWR[2] - real(2) * ln * ny;
+      lW[3] += lWR[3] - real(2) * ln * nz;
+      lW[4] += lWR[4];
+    }
+    prim_vjp(W, lW, ph, lU);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      LWf[((size_t)side * NV + v) * n2 + pq] = lU[v];
+      LWf[((size_t)(S + side) * NV + v) * n2 + pq] = real(0);
+    }
+    return;
+  }
 #pragma unroll
   for (int slot = 0; slot < 2; ++slot) {
     real W[NV], lW[NV], lU[NV] = {0, 0, 0, 0, 0};
@@ -632,7 +684,7 @@ inline AdjScratch adj_layout(const DevMesh& m, void* base, size_t rs) {
 
 template <typename real, int n>
 static cudaError_t rhs_adjoint_n(const DevMesh& m, const real* U, const real* lam, real* out, real scale,
-                                 int accumulate, const Ops<real>& ops, const Phys<real>& ph, void* scratch,
+                                 int accumulate, const Ops<real>& ops, const Phys<real>& ph, void* scratch, double t,
                                  cudaStream_t st) {
   using C = Cfg<n>;
   const int grid = (m.K + C::NE - 1) / C::NE;
@@ -641,10 +693,11 @@ static cudaError_t rhs_adjoint_n(const DevMesh& m, const real* U, const real* la
   cudaError_t err;
   // forward recompute of face states, face gradients and volume gradients
   if ((err = prolong_n<real, n>(m, U, ops, ph, st)) != cudaSuccess) return err;
+  if ((err = launch_bc<real>(m, t, ph, st)) != cudaSuccess) return err;
   if ((err = lift_vol_n<real, n, 0>(m, U, ops, ph, 1, st)) != cudaSuccess) return err;
   k_adj_lamface<real, n><<<grid, C::T, 0, st>>>(lam, (const real*)m.sJ, m.elemSide, (real*)a.LF, m.K, m.S, ops);
   k_adj_face<real, n><<<sgrid, 128, 0, st>>>((const real*)m.Wf, (const real*)m.Gf, (const real*)m.fgeo,
-                                             (const real*)a.LF, (real*)a.LWf, (real*)a.LGf, m.S, ph);
+                                             (const real*)a.LF, (real*)a.LWf, (real*)a.LGf, m.S, m.nBC, ph);
   constexpr size_t smem = adj_vol_smem<real, n>();
   static bool attr = false;
   if (!attr) {
@@ -656,7 +709,8 @@ static cudaError_t rhs_adjoint_n(const DevMesh& m, const real* U, const real* la
   k_adj_vol<real, n><<<grid, C::T, smem, st>>>(U, (const real*)m.Ja, (const real*)m.sJ, (const real*)m.Gvol,
                                                (const real*)m.fgeo, m.elemSide, lam, (const real*)a.LGf,
                                                (real*)a.LWs, (real*)a.muv, m.K, m.S, ops, ph);
-  k_adj_side<real, n><<<sgrid, 128, 0, st>>>((const real*)m.Wf, (const real*)a.LWs, (real*)a.LWf, m.S, ph);
+  k_adj_side<real, n><<<sgrid, 128, 0, st>>>((const real*)m.Wf, (const real*)a.LWs, (const real*)m.fgeo, m.bcKind,
+                                             (real*)a.LWf, m.S, m.nBC, ph);
   k_adj_gather<real, n><<<grid, C::T, 0, st>>>((const real*)a.LWf, m.elemSide, (const real*)a.muv, out, scale,
                                                accumulate, m.K, m.S, ops);
   return cudaGetLastError();
@@ -664,8 +718,8 @@ static cudaError_t rhs_adjoint_n(const DevMesh& m, const real* U, const real* la
 
 template <typename real>
 cudaError_t launch_rhs_adjoint(const DevMesh& m, const real* U, const real* lam, real* out, real scale, int accumulate,
-                               const Ops<real>& ops, const Phys<real>& ph, void* scratch, cudaStream_t st) {
-  FLEXI_DISPATCH_N(m.n, return rhs_adjoint_n<real, NN>(m, U, lam, out, scale, accumulate, ops, ph, scratch, st));
+                               const Ops<real>& ops, const Phys<real>& ph, void* scratch, double t, cudaStream_t st) {
+  FLEXI_DISPATCH_N(m.n, return rhs_adjoint_n<real, NN>(m, U, lam, out, scale, accumulate, ops, ph, scratch, t, st));
   return cudaSuccess;
 }
 

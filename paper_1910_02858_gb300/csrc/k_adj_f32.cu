@@ -3,6 +3,6 @@
 
 namespace flexi {
 template cudaError_t launch_rhs_adjoint<float>(const DevMesh&, const float*, const float*, float*, float, int, const Ops<float>&,
-                                              const Phys<float>&, void*, cudaStream_t);
+                                              const Phys<float>&, void*, double, cudaStream_t);
 template cudaError_t launch_axpby<float>(float*, const float*, float, float, size_t, cudaStream_t);
 }  // namespace flexi

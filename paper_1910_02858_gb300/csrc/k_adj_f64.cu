@@ -3,6 +3,6 @@
 
 namespace flexi {
 template cudaError_t launch_rhs_adjoint<double>(const DevMesh&, const double*, const double*, double*, double, int, const Ops<double>&,
-                                              const Phys<double>&, void*, cudaStream_t);
+                                              const Phys<double>&, void*, double, cudaStream_t);
 template cudaError_t launch_axpby<double>(double*, const double*, double, double, size_t, cudaStream_t);
 }  // namespace flexi

@@ -1,0 +1,111 @@
+"""Discrete adjoint of the CUDA path on meshes with boundaries (exact-state,
+outflow and slip-wall sides; the manufactured source term) against the oracle's
+reverse-mode derivative and a central finite-difference dot-product test."""
+import numpy as np
+import pytest
+import torch
+
+import workloads as wl
+from oracle.dgsem import DGSEM, ROE, Params
+
+from test_gpu_parity import DEV
+
+pytestmark = pytest.mark.gpu
+
+CASES = [
+    # (name, mesh kwargs, N, node_type, riemann, bc_exact, source, kinds)
+    ("mixed_lg_N3_smooth", dict(nelem=(2, 3, 2), Ngeo=3, mapping="sine", reorient_seed=4,
+                                bc_ids=[0, 1, 2, 2, 2, 2]), 3, 0, 2, 1, False, {1: 1, 2: 2}),
+    ("slip_box_lgl_N4_roe", dict(nelem=(2, 2, 2), Ngeo=2, mapping="sine", reorient_seed=2, bc_ids=[2] * 6),
+     4, 1, 0, 1, False, {2: 2}),
+    ("manufactured_lg_N2_exact_outflow", dict(nelem=(3, 2, 2), Ngeo=2, mapping="sine", reorient_seed=1,
+                                              bc_ids=[0, 1, 0, 0, 1, 1]), 2, 0, 2, 2, True, {1: 1}),
+    ("in_out_periodic_yz_N5", dict(nelem=(3, 2, 2), periodic=(False, True, True), reorient_seed=3,
+                                   bc_ids=[0, 1, 0, 0, 0, 0]), 5, 0, 2, 1, False, {1: 1}),
+]
+
+
+def _pair(case):
+    from paper_1910_02858_gb300 import Solver, SolverConfig
+
+    name, mk, N, nt, riem, bc_exact, source, kinds = case
+    mk = dict(dict(lo=(-1,) * 3, hi=(1,) * 3, periodic=(False,) * 3), **mk)
+    mesh = wl.box_mesh(**mk)
+    s = Solver(SolverConfig(N=N, Ngeo=mk.get("Ngeo", 1), node_type=nt, riemann=riem, mu=1 / 400.0,
+                            bc_exact=bc_exact, source=source, adjoint=True), mesh.coords, mesh.conn, device=DEV)
+    for bc_id, kind in kinds.items():
+        s.set_bc(bc_id, kind)
+    dg = DGSEM(Params(N=N, node_type=nt, riemann=ROE, smooth_roe=riem == 2, mu=1 / 400.0, bc_exact=bc_exact,
+                      source=source, bc_kinds=dict(kinds)), mesh.coords, mesh.conn)
+    U0 = wl.perturbed(np.pi * mesh.node_coords(N, nt), seed=7)
+    return s, dg, U0
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_rhs_adjoint_with_boundaries_vs_oracle(case):
+    s, dg, U0 = _pair(case)
+    lam = np.random.default_rng(3).normal(size=U0.shape)
+    out = s.rhs_adjoint(torch.tensor(U0, device=DEV), torch.tensor(lam, device=DEV), 0.3)
+    ref = dg.rhs_vjp(torch.tensor(U0), 0.3, torch.tensor(lam))
+    s.close()
+    d = (out.cpu() - ref).transpose(0, 1).reshape(5, -1).norm(dim=1)
+    r = ref.transpose(0, 1).reshape(5, -1).norm(dim=1)
+    assert float((d / r).max()) < 1e-10, (d / r).tolist()
+
+
+def test_adjoint_step_with_boundaries_vs_oracle():
+    """One reverse LSERK4(5) step from t = 0.2: the exact-state sides and the source
+    are taken at the stage times of the forward step."""
+    s, dg, U0 = _pair(CASES[2])
+    rng = np.random.default_rng(9)
+    lamU0, lamdU0 = rng.normal(size=U0.shape), rng.normal(size=U0.shape)
+    t0, dt = 0.2, 1e-3
+    U = torch.tensor(U0, device=DEV)
+    stages = torch.empty((5,) + U.shape, dtype=U.dtype, device=DEV)
+    s.step_stages(U, torch.zeros_like(U), t0, dt, stages)
+    lamU, lamdU = torch.tensor(lamU0, device=DEV), torch.tensor(lamdU0, device=DEV)
+    s.adjoint_step(stages, lamU, lamdU, t0, dt)
+    st_ref = []
+    dg.rk_step(torch.tensor(U0), torch.zeros_like(torch.tensor(U0)), t0, dt, stages_out=st_ref)
+    rU, _ = dg.adjoint_step(st_ref, torch.tensor(lamU0), torch.tensor(lamdU0), t0, dt)
+    s.close()
+    assert float((lamU.cpu() - rU).norm() / rU.norm()) < 1e-12
+
+
+@pytest.mark.parametrize("case", [CASES[0], CASES[1]], ids=[CASES[0][0], CASES[1][0]])
+def test_dot_product_with_finite_difference_jvp_boundaries(case):
+    """<lam, J v> from a central difference of flexi_rhs equals <J^T lam, v>, with
+    no oracle involved."""
+    s, _, U0 = _pair(case)
+    U0 = torch.tensor(U0, device=DEV)
+    g = torch.Generator(device="cpu").manual_seed(5)
+    v = torch.randn(U0.shape, generator=g, dtype=torch.float64).to(DEV)
+    lam = torch.randn(U0.shape, generator=g, dtype=torch.float64).to(DEV)
+    eps = 1e-6
+    Jv = (s.rhs(U0 + eps * v, 0.1) - s.rhs(U0 - eps * v, 0.1)) / (2 * eps)
+    a = float((lam * Jv).sum())
+    b = float((s.rhs_adjoint(U0, lam, 0.1) * v).sum())
+    s.close()
+    assert abs(a - b) < 1e-6 * abs(b), (a, b)
+
+
+def test_adjoint_with_boundaries_fp32_vs_fp64():
+    """The FP32 form's adjoint on a mesh with boundaries against the FP64 one."""
+    from paper_1910_02858_gb300 import Solver, SolverConfig
+
+    s64, _, U0 = _pair(CASES[0])
+    name, mk, N, nt, riem, bc_exact, source, kinds = CASES[0]
+    mesh = wl.box_mesh(**dict(dict(lo=(-1,) * 3, hi=(1,) * 3, periodic=(False,) * 3), **mk))
+    s32 = Solver(SolverConfig(N=N, Ngeo=mk["Ngeo"], riemann=riem, mu=1 / 400.0, bc_exact=bc_exact, precision=1,
+                              adjoint=True), mesh.coords, mesh.conn, device=DEV)
+    for bc_id, kind in kinds.items():
+        s32.set_bc(bc_id, kind)
+    lam = np.random.default_rng(3).normal(size=U0.shape)
+    a = s64.rhs_adjoint(torch.tensor(U0, device=DEV), torch.tensor(lam, device=DEV), 0.0).cpu()
+    b = s32.rhs_adjoint(torch.tensor(U0, device=DEV, dtype=torch.float32),
+                        torch.tensor(lam, device=DEV, dtype=torch.float32), 0.0).double().cpu()
+    s64.close()
+    s32.close()
+    d = (a - b).transpose(0, 1).reshape(5, -1).norm(dim=1)
+    r = a.transpose(0, 1).reshape(5, -1).norm(dim=1)
+    assert float((d / r).max()) < 1e-4, (d / r).tolist()

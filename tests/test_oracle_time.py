@@ -116,3 +116,26 @@ def test_adjoint_dot_product_forward_mode():
     JTl = dg.rhs_vjp(U0, 0.0, lam)
     a, b = float((lam * Jv).sum()), float((JTl * v).sum())
     assert abs(a - b) < 1e-12 * max(abs(a), 1.0)
+
+
+@pytest.mark.parametrize("kinds", [{1: 1, 2: 2}, {1: 0, 2: 1}])
+def test_adjoint_with_boundaries_matches_central_fd(kinds):
+    """Curved box with exact-state, outflow and slip-wall sides and the
+    manufactured source at t = 0.3: <lam, (L(U + eps v) - L(U - eps v)) / (2 eps)>
+    equals <(dL/dU)^T lam, v> (the outer boundary states depend on the inner
+    ones; the exact state and the source do not).  Kinds: 0 exact state,
+    1 outflow, 2 slip wall; bc_id 0 is always an exact-state side."""
+    N = 2
+    m = wl.box_mesh((2, 2, 2), lo=(-1,) * 3, hi=(1,) * 3, Ngeo=2, mapping="sine", periodic=(False,) * 3,
+                    reorient_seed=3, bc_ids=[0, 1, 2, 2, 1, 2])
+    dg = DGSEM(Params(N=N, riemann=ROE, smooth_roe=True, mu=1.0 / 400.0, bc_exact=2, source=True,
+                      bc_kinds=dict(kinds)), m.coords, m.conn)
+    x = m.node_coords(N, 0)
+    U0 = torch.tensor(wl.perturbed(np.pi * x, seed=3))
+    rng = np.random.default_rng(5)
+    v = torch.tensor(rng.normal(size=U0.shape))
+    lam = torch.tensor(rng.normal(size=U0.shape))
+    eps = 1e-6
+    Jv = (dg.rhs(U0 + eps * v, 0.3) - dg.rhs(U0 - eps * v, 0.3)) / (2 * eps)
+    a, b = float((lam * Jv).sum()), float((dg.rhs_vjp(U0, 0.3, lam) * v).sum())
+    assert abs(a - b) < 1e-7 * abs(b), (a, b)
