@@ -330,12 +330,19 @@ __global__ void k_bc(const double* __restrict__ xbc, const int* __restrict__ bcK
 // ---------------------------------------------------------------------------
 // a2-a4, a6, a7: lifting, gradient prolongation, volume integral
 // ---------------------------------------------------------------------------
+// FP32 CUDA-core form: two CTAs of 512 threads (n = 8) or five of 216 (n = 6) per SM
+template <typename real, int n, int SW>
+constexpr int lift_vol_min_blocks() {
+  if (sizeof(real) != 4 || SW != 0) return 1;
+  return Cfg<n>::T == 512 ? 2 : (Cfg<n>::T == 216 ? 5 : 1);
+}
+
 // SW: 0 line sweeps on the FP32/FP64 pipes; 1 TF32 and 2 BF16 3-term split mma (float only).
 // SPLIT (Gauss-Lobatto, SW = 0 only): the split-form volume integral of Sec. 3.3 with the
-// kinetic-energy-preserving flux (1) or the entropy-conservative flux (2)
-// (Eq. semiDiscreteSplit) with the kinetic-energy-preserving two-point flux.
+// kinetic-energy-preserving two-point flux (1) or the entropy-conservative one (2)
+// (Eq. semiDiscreteSplit).
 template <typename real, int n, int SW, bool LGL, int SPLIT = 0, bool BR2 = false>
-__global__ void __launch_bounds__(Cfg<n>::T, (sizeof(real) == 4 && SW == 0 && Cfg<n>::T == 512) ? 2 : 1) k_lift_vol(
+__global__ void __launch_bounds__(Cfg<n>::T, lift_vol_min_blocks<real, n, SW>()) k_lift_vol(
     const real* __restrict__ U, const real* __restrict__ Ja, const real* __restrict__ sJ,
     const real* __restrict__ Wf, const real* __restrict__ fgeo, const int* __restrict__ elemSide,
     real* __restrict__ Gf, real* __restrict__ Utv, real* __restrict__ Gvol, int K, int S, int bigBase,
@@ -904,7 +911,7 @@ __global__ void __launch_bounds__(128, sizeof(real) == 4 ? 8 : 1) k_face(const r
 // a8-a10: surface integral, -1/J, RK stage update, face states of the new U
 // ---------------------------------------------------------------------------
 template <typename real, int n, int MODE, bool LGL>
-__global__ void __launch_bounds__(Cfg<n>::T, (sizeof(real) == 4 && Cfg<n>::T == 512) ? 3 : 2) k_surf(
+__global__ void __launch_bounds__(Cfg<n>::T, (sizeof(real) == 4 && Cfg<n>::T == 512) ? 4 : ((sizeof(real) == 4 && Cfg<n>::T == 216) ? 8 : 2)) k_surf(
     const real* __restrict__ Ff, const int* __restrict__ elemSide, const real* __restrict__ sJ,
     const real* __restrict__ Utv, real* __restrict__ U, real* __restrict__ dU, real* __restrict__ Ut,
     real* __restrict__ Wf, const double* __restrict__ xsol, RkStage<real> rk, double t, SourceParams src, int K,
