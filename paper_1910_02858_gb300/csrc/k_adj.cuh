@@ -699,13 +699,8 @@ static cudaError_t rhs_adjoint_n(const DevMesh& m, const real* U, const real* la
   k_adj_face<real, n><<<sgrid, 128, 0, st>>>((const real*)m.Wf, (const real*)m.Gf, (const real*)m.fgeo,
                                              (const real*)a.LF, (real*)a.LWf, (real*)a.LGf, m.S, m.nBC, ph);
   constexpr size_t smem = adj_vol_smem<real, n>();
-  static bool attr = false;
-  if (!attr) {
-    if ((err = cudaFuncSetAttribute(k_adj_vol<real, n>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
-        cudaSuccess)
-      return err;
-    attr = true;
-  }
+  static std::atomic<unsigned long long> attr{0};
+  if ((err = ensure_dynamic_smem(k_adj_vol<real, n>, smem, attr)) != cudaSuccess) return err;
   k_adj_vol<real, n><<<grid, C::T, smem, st>>>(U, (const real*)m.Ja, (const real*)m.sJ, (const real*)m.Gvol,
                                                (const real*)m.fgeo, m.elemSide, lam, (const real*)a.LGf,
                                                (real*)a.LWs, (real*)a.muv, m.K, m.S, ops, ph);

@@ -1068,13 +1068,9 @@ static cudaError_t lift_vol_n(const DevMesh& m, const real* U, const Ops<real>& 
                               int store_grad, cudaStream_t st) {
   using C = Cfg<n>;
   constexpr size_t smem = lift_vol_smem<real, n, SW, SPLIT, BR2>();
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t err = cudaFuncSetAttribute(k_lift_vol<real, n, SW, LGL, SPLIT, BR2>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (err != cudaSuccess) return err;
-    attr = true;
-  }
+  static std::atomic<unsigned long long> attr{0};
+  cudaError_t err = ensure_dynamic_smem(k_lift_vol<real, n, SW, LGL, SPLIT, BR2>, smem, attr);
+  if (err != cudaSuccess) return err;
   const int grid = (m.K + C::NE - 1) / C::NE;
   k_lift_vol<real, n, SW, LGL, SPLIT, BR2><<<grid, C::T, smem, st>>>(U, (const real*)m.Ja, (const real*)m.sJ,
                                                          (const real*)m.Wf, (const real*)m.fgeo, m.elemSide,

@@ -4,9 +4,26 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "dg_common.cuh"
 
 namespace flexi {
+
+// Raises a kernel's dynamic shared-memory limit to smem bytes once per device
+// (the attribute is per device; done holds one bit per device ordinal < 64, and
+// larger ordinals set it on every call).  Safe to call from several host threads.
+template <typename Kernel>
+cudaError_t ensure_dynamic_smem(Kernel* kernel, size_t smem, std::atomic<unsigned long long>& done) {
+  int dev = 0;
+  cudaError_t err = cudaGetDevice(&dev);
+  if (err != cudaSuccess) return err;
+  const unsigned long long bit = dev < 64 ? 1ull << dev : 0ull;
+  if (bit != 0 && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+  err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err == cudaSuccess && bit != 0) done.fetch_or(bit, std::memory_order_release);
+  return err;
+}
 
 // Device-resident mesh, geometry and scratch of one context (type-erased).
 struct DevMesh {
