@@ -772,7 +772,6 @@ flexi_status flexi_rk_step_stages(flexi_ctx* c, void* U, void* dU, double t, dou
 
 static bool adjoint_supported(const flexi_ctx* c) {
   return c->p.adjoint && c->p.lifting == FLEXI_LIFTING_BR1 && c->nMortar == 0 &&
-         (c->p.riemann == FLEXI_RIEMANN_ROE || c->p.riemann == FLEXI_RIEMANN_ROE_SMOOTH) &&
          c->p.split_form == FLEXI_SPLIT_STANDARD;
 }
 

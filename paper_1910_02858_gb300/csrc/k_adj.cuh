@@ -1,7 +1,9 @@
 // Discrete adjoint of the right-hand side: mu = (dL/dU)^T lam, by hand-written
 // reverse mode of every step of the forward operator (steps a1..a9 of k_dg.cuh),
-// for the Roe flux (optionally with smoothed |lambda|), BR1 lifting and the
-// standard volume integral, on periodic meshes and meshes with boundary sides.
+// for BR1 lifting and the standard volume integral, on periodic meshes and
+// meshes with boundary sides.  Numerical flux: the Roe fluxes have a hand-written
+// reverse; HLLC, Rusanov and the entropy-conservative flux are differentiated in
+// forward mode (dual numbers, ten tangents per face node).
 // Boundary sides: the outer state is a function of the inner one (outflow: the
 // same state; slip wall: normal velocity reversed, a reflection; exact state:
 // independent of U) and the outer gradient is the inner one, so their adjoints
@@ -271,6 +273,100 @@ __device__ __forceinline__ void roe_vjp(const real WL[NV], const real WR[NV], co
 }
 
 // ---------------------------------------------------------------------------
+// reverse of the other numerical fluxes by forward-mode differentiation
+// ---------------------------------------------------------------------------
+// Dual number x + dx eps (eps^2 = 0): the templated flux functions of
+// dg_common.cuh evaluated on Dual<real> give their directional derivative.
+template <typename r>
+struct Dual {
+  r v, d;
+  Dual() = default;
+  __device__ constexpr Dual(double x) : v(r(x)), d(r(0)) {}
+  __device__ constexpr Dual(r x, r dx) : v(x), d(dx) {}
+  friend __device__ Dual operator+(Dual a, Dual b) { return Dual(a.v + b.v, a.d + b.d); }
+  friend __device__ Dual operator-(Dual a, Dual b) { return Dual(a.v - b.v, a.d - b.d); }
+  friend __device__ Dual operator-(Dual a) { return Dual(-a.v, -a.d); }
+  friend __device__ Dual operator*(Dual a, Dual b) { return Dual(a.v * b.v, a.d * b.v + a.v * b.d); }
+  friend __device__ Dual operator/(Dual a, Dual b) {
+    const r q = a.v / b.v;
+    return Dual(q, (a.d - q * b.d) / b.v);
+  }
+  __device__ Dual& operator+=(Dual b) { return *this = *this + b; }
+  __device__ Dual& operator-=(Dual b) { return *this = *this - b; }
+  __device__ Dual& operator*=(Dual b) { return *this = *this * b; }
+  friend __device__ bool operator<(Dual a, Dual b) { return a.v < b.v; }
+  friend __device__ bool operator>(Dual a, Dual b) { return a.v > b.v; }
+  friend __device__ bool operator<=(Dual a, Dual b) { return a.v <= b.v; }
+  friend __device__ bool operator>=(Dual a, Dual b) { return a.v >= b.v; }
+};
+
+template <typename r>
+__device__ __forceinline__ Dual<r> dg_sqrt(Dual<r> x) {
+  const r s = dg_sqrt(x.v);
+  return Dual<r>(s, x.d / (r(2) * s));
+}
+template <typename r>
+__device__ __forceinline__ Dual<r> dg_log(Dual<r> x) {
+  return Dual<r>(dg_log(x.v), x.d / x.v);
+}
+// min / max: the derivative of the selected argument
+template <typename r>
+__device__ __forceinline__ Dual<r> fmin(Dual<r> a, Dual<r> b) {
+  return b.v < a.v ? b : a;
+}
+template <typename r>
+__device__ __forceinline__ Dual<r> fmax(Dual<r> a, Dual<r> b) {
+  return b.v > a.v ? b : a;
+}
+
+template <typename r>
+__device__ __forceinline__ Phys<Dual<r>> dual_phys(const Phys<r>& p) {
+  Phys<Dual<r>> q;
+  q.gamma = Dual<r>(p.gamma, r(0));
+  q.gm1 = Dual<r>(p.gm1, r(0));
+  q.inv_gm1 = Dual<r>(p.inv_gm1, r(0));
+  q.mu = Dual<r>(p.mu, r(0));
+  q.lam_th = Dual<r>(p.lam_th, r(0));
+  q.Ma = Dual<r>(p.Ma, r(0));
+  q.eta_br2 = Dual<r>(p.eta_br2, r(0));
+  q.riemann = p.riemann;
+  q.bc_exact = p.bc_exact;
+  return q;
+}
+
+// lamWL += (df/dWL)^T lamf, lamWR += (df/dWR)^T lamf for the flux ph.riemann
+// (HLLC, Rusanov, entropy-conservative; the Roe fluxes have roe_vjp): one
+// dual-number evaluation per input component, each dotted with lamf.  Branches
+// (wave-speed min/max, the HLLC star regions) follow the forward evaluation.
+template <typename real>
+__device__ void riemann_vjp_dual(const real WL[NV], const real WR[NV], const real n[3], const Phys<real>& ph,
+                                 const real lf[NV], real lWL[NV], real lWR[NV]) {
+  using D = Dual<real>;
+  const Phys<D> pd = dual_phys(ph);
+  const D nd[3] = {D(n[0], real(0)), D(n[1], real(0)), D(n[2], real(0))};
+  real g[2 * NV];
+#pragma unroll 1
+  for (int j = 0; j < 2 * NV; ++j) {
+    D a[NV], b[NV], f[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      a[v] = D(WL[v], j == v ? real(1) : real(0));
+      b[v] = D(WR[v], j == NV + v ? real(1) : real(0));
+    }
+    riemann(a, b, nd, pd, f);
+    real s = real(0);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) s += lf[v] * f[v].d;
+    g[j] = s;
+  }
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    lWL[v] += g[v];
+    lWR[v] += g[NV + v];
+  }
+}
+
+// ---------------------------------------------------------------------------
 // kernels
 // ---------------------------------------------------------------------------
 template <typename real, int n>
@@ -317,7 +413,9 @@ __global__ void __launch_bounds__(Cfg<n>::T) k_adj_lamface(const real* __restric
   }
 }
 
-template <typename real, int n>
+// DUAL: the flux reverse by dual numbers (HLLC, Rusanov, entropy-conservative);
+// otherwise the hand-written Roe reverse.
+template <typename real, int n, bool DUAL>
 __global__ void __launch_bounds__(128) k_adj_face(const real* __restrict__ Wf, const real* __restrict__ Gf,
                                                   const real* __restrict__ fgeo, const real* __restrict__ LF,
                                                   real* __restrict__ LWf, real* __restrict__ LGf, int S, int nBC,
@@ -347,7 +445,10 @@ __global__ void __launch_bounds__(128) k_adj_face(const real* __restrict__ Wf, c
   real lGL[15], lGR[15];
 #pragma unroll
   for (int c = 0; c < 15; ++c) lGL[c] = lGR[c] = real(0);
-  roe_vjp(WL, WR, nv, ph, ph.riemann == 2, lf, lWL, lWR);
+  if constexpr (DUAL)
+    riemann_vjp_dual(WL, WR, nv, ph, lf, lWL, lWR);
+  else
+    roe_vjp(WL, WR, nv, ph, ph.riemann == 2, lf, lWL, lWR);
   real lF[3][NV];
 #pragma unroll
   for (int d = 0; d < 3; ++d)
@@ -696,8 +797,12 @@ static cudaError_t rhs_adjoint_n(const DevMesh& m, const real* U, const real* la
   if ((err = launch_bc<real>(m, t, ph, st)) != cudaSuccess) return err;
   if ((err = lift_vol_n<real, n, 0>(m, U, ops, ph, 1, st)) != cudaSuccess) return err;
   k_adj_lamface<real, n><<<grid, C::T, 0, st>>>(lam, (const real*)m.sJ, m.elemSide, (real*)a.LF, m.K, m.S, ops);
-  k_adj_face<real, n><<<sgrid, 128, 0, st>>>((const real*)m.Wf, (const real*)m.Gf, (const real*)m.fgeo,
-                                             (const real*)a.LF, (real*)a.LWf, (real*)a.LGf, m.S, m.nBC, ph);
+  if (ph.riemann == 0 || ph.riemann == 2)
+    k_adj_face<real, n, false><<<sgrid, 128, 0, st>>>((const real*)m.Wf, (const real*)m.Gf, (const real*)m.fgeo,
+                                                      (const real*)a.LF, (real*)a.LWf, (real*)a.LGf, m.S, m.nBC, ph);
+  else
+    k_adj_face<real, n, true><<<sgrid, 128, 0, st>>>((const real*)m.Wf, (const real*)m.Gf, (const real*)m.fgeo,
+                                                     (const real*)a.LF, (real*)a.LWf, (real*)a.LGf, m.S, m.nBC, ph);
   constexpr size_t smem = adj_vol_smem<real, n>();
   static std::atomic<unsigned long long> attr{0};
   if ((err = ensure_dynamic_smem(k_adj_vol<real, n>, smem, attr)) != cudaSuccess) return err;

@@ -1,19 +1,23 @@
 """Discrete adjoint of the CUDA path on meshes with boundaries (exact-state,
-outflow and slip-wall sides; the manufactured source term) against the oracle's
-reverse-mode derivative and a central finite-difference dot-product test."""
+outflow and slip-wall sides; the manufactured source term) and with the HLLC,
+Rusanov and entropy-conservative fluxes (reversed by dual numbers) against the
+oracle's reverse-mode derivative and central finite-difference dot-product tests."""
 import numpy as np
 import pytest
 import torch
 
 import workloads as wl
-from oracle.dgsem import DGSEM, ROE, Params
+from oracle.dgsem import DGSEM, EC, HLLC, ROE, RUSANOV, Params
+
+RIEM = {0: ROE, 1: HLLC, 2: ROE, 3: RUSANOV, 4: EC}
 
 from test_gpu_parity import DEV
 
 pytestmark = pytest.mark.gpu
 
 CASES = [
-    # (name, mesh kwargs, N, node_type, riemann, bc_exact, source, kinds)
+    # (name, mesh kwargs, N, node_type, riemann (0 Roe, 1 HLLC, 2 smoothed Roe, 3 Rusanov, 4 EC),
+    #  bc_exact, source, kinds)
     ("mixed_lg_N3_smooth", dict(nelem=(2, 3, 2), Ngeo=3, mapping="sine", reorient_seed=4,
                                 bc_ids=[0, 1, 2, 2, 2, 2]), 3, 0, 2, 1, False, {1: 1, 2: 2}),
     ("slip_box_lgl_N4_roe", dict(nelem=(2, 2, 2), Ngeo=2, mapping="sine", reorient_seed=2, bc_ids=[2] * 6),
@@ -22,6 +26,14 @@ CASES = [
                                               bc_ids=[0, 1, 0, 0, 1, 1]), 2, 0, 2, 2, True, {1: 1}),
     ("in_out_periodic_yz_N5", dict(nelem=(3, 2, 2), periodic=(False, True, True), reorient_seed=3,
                                    bc_ids=[0, 1, 0, 0, 0, 0]), 5, 0, 2, 1, False, {1: 1}),
+    ("hllc_mixed_lg_N3", dict(nelem=(2, 3, 2), Ngeo=3, mapping="sine", reorient_seed=4,
+                              bc_ids=[0, 1, 2, 2, 2, 2]), 3, 0, 1, 1, False, {1: 1, 2: 2}),
+    ("hllc_periodic_lg_N4", dict(nelem=(2, 2, 3), periodic=(True,) * 3, reorient_seed=5), 4, 0, 1, 1, False, {}),
+    ("rusanov_slip_lgl_N3", dict(nelem=(2, 2, 2), Ngeo=2, mapping="sine", reorient_seed=2, bc_ids=[2] * 6),
+     3, 1, 3, 1, False, {2: 2}),
+    ("ec_periodic_lgl_N3", dict(nelem=(2, 3, 2), periodic=(True,) * 3, reorient_seed=6), 3, 1, 4, 1, False, {}),
+    ("hllc_manufactured_N2", dict(nelem=(3, 2, 2), Ngeo=2, mapping="sine", reorient_seed=1,
+                                  bc_ids=[0, 1, 0, 0, 1, 1]), 2, 0, 1, 2, True, {1: 1}),
 ]
 
 
@@ -35,7 +47,7 @@ def _pair(case):
                             bc_exact=bc_exact, source=source, adjoint=True), mesh.coords, mesh.conn, device=DEV)
     for bc_id, kind in kinds.items():
         s.set_bc(bc_id, kind)
-    dg = DGSEM(Params(N=N, node_type=nt, riemann=ROE, smooth_roe=riem == 2, mu=1 / 400.0, bc_exact=bc_exact,
+    dg = DGSEM(Params(N=N, node_type=nt, riemann=RIEM[riem], smooth_roe=riem == 2, mu=1 / 400.0, bc_exact=bc_exact,
                       source=source, bc_kinds=dict(kinds)), mesh.coords, mesh.conn)
     U0 = wl.perturbed(np.pi * mesh.node_coords(N, nt), seed=7)
     return s, dg, U0
@@ -53,10 +65,11 @@ def test_rhs_adjoint_with_boundaries_vs_oracle(case):
     assert float((d / r).max()) < 1e-10, (d / r).tolist()
 
 
-def test_adjoint_step_with_boundaries_vs_oracle():
+@pytest.mark.parametrize("ci", [2, 8], ids=[CASES[2][0], CASES[8][0]])
+def test_adjoint_step_with_boundaries_vs_oracle(ci):
     """One reverse LSERK4(5) step from t = 0.2: the exact-state sides and the source
     are taken at the stage times of the forward step."""
-    s, dg, U0 = _pair(CASES[2])
+    s, dg, U0 = _pair(CASES[ci])
     rng = np.random.default_rng(9)
     lamU0, lamdU0 = rng.normal(size=U0.shape), rng.normal(size=U0.shape)
     t0, dt = 0.2, 1e-3
@@ -72,7 +85,8 @@ def test_adjoint_step_with_boundaries_vs_oracle():
     assert float((lamU.cpu() - rU).norm() / rU.norm()) < 1e-12
 
 
-@pytest.mark.parametrize("case", [CASES[0], CASES[1]], ids=[CASES[0][0], CASES[1][0]])
+@pytest.mark.parametrize("case", [CASES[0], CASES[1], CASES[4], CASES[6]],
+                         ids=[CASES[0][0], CASES[1][0], CASES[4][0], CASES[6][0]])
 def test_dot_product_with_finite_difference_jvp_boundaries(case):
     """<lam, J v> from a central difference of flexi_rhs equals <J^T lam, v>, with
     no oracle involved."""
