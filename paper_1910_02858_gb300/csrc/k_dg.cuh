@@ -330,23 +330,30 @@ __global__ void k_bc(const double* __restrict__ xbc, const int* __restrict__ bcK
 // ---------------------------------------------------------------------------
 // a2-a4, a6, a7: lifting, gradient prolongation, volume integral
 // ---------------------------------------------------------------------------
-// FP32 CUDA-core form: two CTAs of 512 threads (n = 8) or five of 216 (n = 6) per SM
-template <typename real, int n, int SW>
+// Resident CTAs per SM asked of the register allocator, from measurements: FP32
+// CUDA-core form two of 512 threads at n = 8 and five of 216 at n = 6 (standard
+// form); FP64 an explicit minimum of one, which lets the compiler take more
+// registers (about 1 % faster at n = 6 and 8); 0: the compiler's default
+// (k_lift_vol without a minimum; an explicit minimum of one halved the occupancy
+// of the tensor-core forms).
+template <typename real, int n, int SW, int SPLIT, bool BR2>
 constexpr int lift_vol_min_blocks() {
-  if (sizeof(real) != 4 || SW != 0) return 1;
-  return Cfg<n>::T == 512 ? 2 : (Cfg<n>::T == 216 ? 5 : 1);
+  if (sizeof(real) == 8) return 1;
+  if (SW != 0) return 0;
+  if (Cfg<n>::T == 512) return 2;
+  return (Cfg<n>::T == 216 && SPLIT == 0 && !BR2) ? 5 : 0;
 }
 
 // SW: 0 line sweeps on the FP32/FP64 pipes; 1 TF32 and 2 BF16 3-term split mma (float only).
 // SPLIT (Gauss-Lobatto, SW = 0 only): the split-form volume integral of Sec. 3.3 with the
 // kinetic-energy-preserving two-point flux (1) or the entropy-conservative one (2)
 // (Eq. semiDiscreteSplit).
-template <typename real, int n, int SW, bool LGL, int SPLIT = 0, bool BR2 = false>
-__global__ void __launch_bounds__(Cfg<n>::T, lift_vol_min_blocks<real, n, SW>()) k_lift_vol(
+template <typename real, int n, int SW, bool LGL, int SPLIT, bool BR2>
+__device__ __forceinline__ void lift_vol_body(
     const real* __restrict__ U, const real* __restrict__ Ja, const real* __restrict__ sJ,
     const real* __restrict__ Wf, const real* __restrict__ fgeo, const int* __restrict__ elemSide,
     real* __restrict__ Gf, real* __restrict__ Utv, real* __restrict__ Gvol, int K, int S, int bigBase,
-    const real* __restrict__ QB, Ops<real> ops, Phys<real> ph) {
+    const real* __restrict__ QB, const Ops<real>& ops, const Phys<real>& ph) {
   using C = Cfg<n>;
   constexpr int n2 = C::n2, n3 = C::n3, NE = C::NE, T = C::T, n3p = C::n3p;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -859,6 +866,35 @@ __global__ void __launch_bounds__(Cfg<n>::T, lift_vol_min_blocks<real, n, SW>())
   }
 }
 
+#define FLEXI_LIFT_VOL_PARAMS                                                                              \
+  const real *__restrict__ U, const real *__restrict__ Ja, const real *__restrict__ sJ,                   \
+      const real *__restrict__ Wf, const real *__restrict__ fgeo, const int *__restrict__ elemSide,        \
+      real *__restrict__ Gf, real *__restrict__ Utv, real *__restrict__ Gvol, int K, int S, int bigBase, \
+      const real *__restrict__ QB, Ops<real> ops, Phys<real> ph
+#define FLEXI_LIFT_VOL_ARGS U, Ja, sJ, Wf, fgeo, elemSide, Gf, Utv, Gvol, K, S, bigBase, QB, ops, ph
+
+// the kernel at the compiler's default register allocation
+template <typename real, int n, int SW, bool LGL, int SPLIT = 0, bool BR2 = false>
+__global__ void __launch_bounds__(Cfg<n>::T) k_lift_vol(FLEXI_LIFT_VOL_PARAMS) {
+  lift_vol_body<real, n, SW, LGL, SPLIT, BR2>(FLEXI_LIFT_VOL_ARGS);
+}
+
+// the same kernel with lift_vol_min_blocks() CTAs per SM (register cap)
+template <typename real, int n, int SW, bool LGL, int SPLIT = 0, bool BR2 = false>
+__global__ void __launch_bounds__(Cfg<n>::T, lift_vol_min_blocks<real, n, SW, SPLIT, BR2>()) k_lift_vol_mb(FLEXI_LIFT_VOL_PARAMS) {
+  lift_vol_body<real, n, SW, LGL, SPLIT, BR2>(FLEXI_LIFT_VOL_ARGS);
+}
+#undef FLEXI_LIFT_VOL_PARAMS
+#undef FLEXI_LIFT_VOL_ARGS
+
+template <typename real, int n, int SW, bool LGL, int SPLIT, bool BR2>
+constexpr auto lift_vol_kernel() {
+  if constexpr (lift_vol_min_blocks<real, n, SW, SPLIT, BR2>() > 0)
+    return &k_lift_vol_mb<real, n, SW, LGL, SPLIT, BR2>;
+  else
+    return &k_lift_vol<real, n, SW, LGL, SPLIT, BR2>;
+}
+
 template <typename real, int n, int SW, int SPLIT = 0, bool BR2 = false>
 constexpr size_t lift_vol_smem() {
   using C = Cfg<n>;
@@ -1068,11 +1104,12 @@ static cudaError_t lift_vol_n(const DevMesh& m, const real* U, const Ops<real>& 
                               int store_grad, cudaStream_t st) {
   using C = Cfg<n>;
   constexpr size_t smem = lift_vol_smem<real, n, SW, SPLIT, BR2>();
+  auto* kernel = lift_vol_kernel<real, n, SW, LGL, SPLIT, BR2>();
   static std::atomic<unsigned long long> attr{0};
-  cudaError_t err = ensure_dynamic_smem(k_lift_vol<real, n, SW, LGL, SPLIT, BR2>, smem, attr);
+  cudaError_t err = ensure_dynamic_smem(kernel, smem, attr);
   if (err != cudaSuccess) return err;
   const int grid = (m.K + C::NE - 1) / C::NE;
-  k_lift_vol<real, n, SW, LGL, SPLIT, BR2><<<grid, C::T, smem, st>>>(U, (const real*)m.Ja, (const real*)m.sJ,
+  kernel<<<grid, C::T, smem, st>>>(U, (const real*)m.Ja, (const real*)m.sJ,
                                                          (const real*)m.Wf, (const real*)m.fgeo, m.elemSide,
                                                          (real*)m.Gf, (real*)m.Utv,
                                                          store_grad ? (real*)m.Gvol : nullptr, m.K, m.S,
