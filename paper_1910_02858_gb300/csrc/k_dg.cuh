@@ -54,7 +54,7 @@ __device__ __forceinline__ void line_sweep3(const real* __restrict__ buf, real* 
   for (int l = 0; l < 3; ++l) {
     const int stride = l == 0 ? 1 : (l == 1 ? P : P * n);
     for (int it = tid; it < L; it += T) {
-      const int el = it / (NV * n2);
+      const int el = NE == 1 ? 0 : it / (NV * n2);  // it < L: one element per CTA for n >= 4
       const int r = it - el * NV * n2;
       const int v = r / n2, line = r - v * n2;
       const int a0 = line % n, a1 = line / n;  // free indices in increasing direction order
@@ -101,9 +101,9 @@ template <typename real, int n, bool LGL, int l>
 __device__ __forceinline__ void lift_line(const real* __restrict__ buf, real* __restrict__ out,
                                           const real* __restrict__ Q, const Ops<real>& ops, int it) {
   using C = Cfg<n>;
-  constexpr int n2 = C::n2, n3p = C::n3p, P = C::P;
+  constexpr int n2 = C::n2, n3p = C::n3p, P = C::P, NE = C::NE;
   constexpr int stride = l == 0 ? 1 : (l == 1 ? P : P * n);
-  const int el = it / (15 * n2);
+  const int el = NE == 1 ? 0 : it / (15 * n2);
   const int r = it - el * 15 * n2;
   const int c = r / n2, line = r - c * n2;
   const int d = c / NV, v = c - d * NV;
@@ -368,6 +368,8 @@ __device__ __forceinline__ void lift_vol_body(
   real* sSJ = sJm + (BR2 ? NE * 6 * 15 * n2 : 0);                          // BR2: [NE][n3p] 1/J
   real* sOp = sSJ + (BR2 ? NE * n3p : 0);  // DhatT, lm, lp, lhm, lhp (+ DT)
   int* sES = reinterpret_cast<int*>(sOp + n2 + 4 * n + (SPLIT ? n2 : 0));
+  int* sSlot = sES + NE * 6;   // [NE][6] side slot (slave * S + side) of each face
+  int* sMpq = sSlot + NE * 6;  // [NE][6][n2] master-frame node of each face node
   static_assert(!SPLIT || (LGL && SW == 0), "the split form is built on Gauss-Lobatto nodes with CUDA-core sweeps");
   static_assert(!BR2 || (SW == 0 && !SPLIT), "BR2 face gradients are built for the standard form, CUDA-core sweeps");
 
@@ -382,7 +384,11 @@ __device__ __forceinline__ void lift_vol_body(
   load_ops<real, n>(sOp, ops, tid, T);
   if constexpr (SPLIT)
     for (int t = tid; t < n2; t += T) sOp[n2 + 4 * n + t] = ops.DT[t];
-  for (int t = tid; t < NE * 6; t += T) sES[t] = (e0 + t / 6 < K) ? elemSide[(size_t)e0 * 6 + t] : 0;
+  for (int t = tid; t < NE * 6; t += T) {
+    const int es = (e0 + t / 6 < K) ? elemSide[(size_t)e0 * 6 + t] : 0;
+    sES[t] = es;
+    sSlot[t] = es_slave(es) * S + es_side(es);
+  }
 
   real Uo[NV], W[NV], jac[9], sj;
   if (valid) {
@@ -412,6 +418,7 @@ __device__ __forceinline__ void lift_vol_body(
     const int es = sES[el2 * 6 + s];
     const int side = es_side(es);
     const int mpq = orient_pq(es_orient(es), n - 1, pq % n, pq / n);
+    sMpq[it] = mpq;  // reused by the gradient prolongation
     const real* w0 = Wf + ((size_t)side * NV) * n2 + mpq;
     const real* w1 = Wf + ((size_t)(S + side) * NV) * n2 + mpq;
     const real* g = fgeo + ((size_t)side * 4) * n2 + mpq;
@@ -593,7 +600,7 @@ __device__ __forceinline__ void lift_vol_body(
 #pragma unroll
     for (int l = 0; l < 3; ++l)
     for (int it = tid; it < NE * 15 * n2; it += T) {
-      const int el2 = it / (15 * n2);
+      const int el2 = NE == 1 ? 0 : it / (15 * n2);
       const int r = it - el2 * 15 * n2;
       const int c = r / n2, line = r - c * n2;
       if (e0 + el2 >= K) continue;
@@ -619,9 +626,8 @@ __device__ __forceinline__ void lift_vol_body(
       }
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        const int es = sES[el2 * 6 + 2 * l + h];
-        const int mpq = orient_pq(es_orient(es), n - 1, p, q);
-        Gf[((size_t)(es_slave(es) * S + es_side(es)) * 15 + c) * n2 + mpq] = h ? gp : gm;
+        const int f = el2 * 6 + 2 * l + h;
+        Gf[((size_t)sSlot[f] * 15 + c) * n2 + sMpq[f * n2 + line]] = h ? gp : gm;
       }
     }
   }
@@ -906,7 +912,7 @@ constexpr size_t lift_vol_smem() {
   return sizeof(real) * (C::NE * 15 * C::n3p + out + C::NE * 6 * 15 * C::n2 + C::n2 + 4 * n +
                          (SPLIT ? C::n2 : 0) + ((SPLIT && sizeof(real) == 8) ? C::NE * 3 * NV * C::n3p : 0) +
                          (BR2 ? C::NE * 6 * 15 * C::n2 + C::NE * C::n3p : 0)) +
-         sizeof(int) * C::NE * 6;
+         sizeof(int) * (C::NE * 12 + C::NE * 6 * C::n2);
 }
 
 // ---------------------------------------------------------------------------
