@@ -83,7 +83,7 @@ enum { FLEXI_BC_EXACT = 0, FLEXI_BC_OUTFLOW = 1, FLEXI_BC_SLIP_WALL = 2 };
  * volume integral and, averaged, in the viscous face flux.  BR2 keeps that volume gradient,
  * but the viscous face flux takes on each side the broken gradient (the BR1 gradient minus
  * the lifting r_f = (1/J) l_hat(+-1) (U* - U_e) n s_hat of every face) plus eta_br2 times
- * the face's own lifting (FP64 / FP32, standard volume integral; no adjoint). */
+ * the face's own lifting (FP64 / FP32, standard volume integral). */
 enum { FLEXI_LIFTING_BR1 = 0, FLEXI_LIFTING_BR2 = 1 };
 /* Exact states for exact-state boundary sides (and the manufactured source term). */
 enum { FLEXI_EXACT_TGV = 0, FLEXI_EXACT_FREESTREAM = 1, FLEXI_EXACT_MANUFACTURED = 2 };
@@ -181,8 +181,8 @@ flexi_status flexi_rk_step_stages(flexi_ctx *ctx, void *U, void *dU, double t, d
  * U_stages: device [5][K][5][n^3] as written by flexi_rk_step_stages; t: the
  * step's start time (exact-state boundaries are evaluated at the stage times of
  * the forward step).  lamU, lam_dU: device, updated in place.  Requires
- * flexi_params.adjoint = 1, FLEXI_FP64 or FLEXI_FP32, BR1 lifting and the
- * standard volume integral; every numerical flux (the Roe fluxes by a
+ * flexi_params.adjoint = 1, FLEXI_FP64 or FLEXI_FP32, BR1 or BR2 lifting and
+ * the standard volume integral; every numerical flux (the Roe fluxes by a
  * hand-written reverse, HLLC, Rusanov and EC in forward mode); periodic meshes
  * and meshes with boundaries of every kind (the outer state's dependence on the
  * inner one is transposed; a source term does not depend on U); no mortars

@@ -1,6 +1,6 @@
 // Discrete adjoint of the right-hand side: mu = (dL/dU)^T lam, by hand-written
 // reverse mode of every step of the forward operator (steps a1..a9 of k_dg.cuh),
-// for BR1 lifting and the standard volume integral, on periodic meshes and
+// for BR1 or BR2 lifting and the standard volume integral, on periodic meshes and
 // meshes with boundary sides.  Numerical flux: the Roe fluxes have a hand-written
 // reverse; HLLC, Rusanov and the entropy-conservative flux are differentiated in
 // forward mode (dual numbers, ten tangents per face node).
@@ -495,24 +495,32 @@ __device__ __forceinline__ real dhatT_line(const real* __restrict__ sD, const re
 }
 
 template <typename real, int n>
-constexpr size_t adj_vol_smem() {
+constexpr size_t adj_vol_smem(bool br2) {
   using C = Cfg<n>;
-  return sizeof(real) * (C::NE * 15 * C::n3 + C::NE * 6 * 15 * C::n2 + C::n2 + 4 * n) + sizeof(int) * C::NE * 8;
+  return sizeof(real) * (C::NE * 15 * C::n3 + C::NE * 6 * 15 * C::n2 + C::n2 + 4 * n +
+                         (br2 ? C::NE * C::n3 + C::NE * 6 * NV * C::n2 : 0)) +
+         sizeof(int) * C::NE * 8;
 }
 
-template <typename real, int n>
+// BR2: the face gradients are the broken gradient G - sum_f r_f plus eta r_s of
+// the face's own lifting, r_f = (1/J) l_hat_f Jm_f with the jump
+// Jm_f = (U* - W_own) n s_hat; their adjoints reach U* (added to LWs) and the
+// element's own face state (added to its slot of LWf, written by k_adj_face).
+template <typename real, int n, bool BR2>
 __global__ void __launch_bounds__(Cfg<n>::T) k_adj_vol(
     const real* __restrict__ U, const real* __restrict__ Ja, const real* __restrict__ sJ, const real* __restrict__ Gvol,
     const real* __restrict__ fgeo, const int* __restrict__ elemSide, const real* __restrict__ lam,
-    const real* __restrict__ LGf, real* __restrict__ LWs, real* __restrict__ muv, int K, int S, Ops<real> ops,
-    Phys<real> ph) {
+    const real* __restrict__ LGf, real* __restrict__ LWs, real* __restrict__ LWf, real* __restrict__ muv, int K, int S,
+    Ops<real> ops, Phys<real> ph) {
   using C = Cfg<n>;
   constexpr int n2 = C::n2, n3 = C::n3, NE = C::NE, T = C::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   real* sbuf = reinterpret_cast<real*>(smem_raw);  // [NE][15][n3]
   real* sF = sbuf + NE * 15 * n3;                  // [NE][6][15][n2] face-gradient adjoints
   real* sOp = sF + NE * 6 * 15 * n2;
-  int* sES = reinterpret_cast<int*>(sOp + n2 + 4 * n);
+  real* sSJ = sOp + n2 + 4 * n;                 // BR2: [NE][n3] 1/J
+  real* sBr = sSJ + (BR2 ? NE * n3 : 0);        // BR2: [NE][6][5][n2] adjoint of U* from the jumps
+  int* sES = reinterpret_cast<int*>(sBr + (BR2 ? NE * 6 * NV * n2 : 0));
   const int tid = threadIdx.x;
   const int el = tid / n3, node = tid - el * n3;
   const int e0 = blockIdx.x * NE;
@@ -589,11 +597,60 @@ __global__ void __launch_bounds__(Cfg<n>::T) k_adj_vol(
     const real* Fe = sF + el * 6 * 15 * n2;
     const int pq0 = j + n * k, pq1 = i + n * k, pq2 = i + n * j;
     const real c0 = lm[i], c1 = lp[i], c2 = lm[j], c3 = lp[j], c4 = lm[k], c5 = lp[k];
+    real B[15];
 #pragma unroll
     for (int c = 0; c < 15; ++c) {
-      lamG[c] += c0 * Fe[(0 * 15 + c) * n2 + pq0] + c1 * Fe[(1 * 15 + c) * n2 + pq0] +
-                 c2 * Fe[(2 * 15 + c) * n2 + pq1] + c3 * Fe[(3 * 15 + c) * n2 + pq1] +
-                 c4 * Fe[(4 * 15 + c) * n2 + pq2] + c5 * Fe[(5 * 15 + c) * n2 + pq2];
+      B[c] = c0 * Fe[(0 * 15 + c) * n2 + pq0] + c1 * Fe[(1 * 15 + c) * n2 + pq0] +
+             c2 * Fe[(2 * 15 + c) * n2 + pq1] + c3 * Fe[(3 * 15 + c) * n2 + pq1] +
+             c4 * Fe[(4 * 15 + c) * n2 + pq2] + c5 * Fe[(5 * 15 + c) * n2 + pq2];
+      lamG[c] += B[c];
+    }
+    if constexpr (BR2) {
+      // adjoint of the liftings r_f in the broken gradient: (1/J) times the
+      // prolongation^T B of the face-gradient adjoints, reduced along each face's lines
+      __syncthreads();  // the a7 reverse has read lam_vol from the buffer
+#pragma unroll
+      for (int c = 0; c < 15; ++c) myb[c * n3 + node] = B[c] * sj;
+      sSJ[el * n3 + node] = sj;
+      __syncthreads();
+      const real* lhm = sOp + n2 + 2 * n;
+      const real* lhp = sOp + n2 + 3 * n;
+      for (int it = tid; it < NE * 6 * n2; it += T) {
+        const int el2 = it / (6 * n2);
+        const int r = it - el2 * 6 * n2;
+        const int s = r / n2, pq = r - s * n2;
+        if (e0 + el2 >= K) continue;
+        const int l = s >> 1;
+        const real* lv = (s & 1) ? lhp : lhm;  // l_hat(+-1)
+        const real* lw = (s & 1) ? lp : lm;    // l(+-1)
+        const int p = pq % n, q = pq / n;
+        const int es = sES[el2 * 6 + s];
+        const int side = es_side(es);
+        const int mpq = orient_pq(es_orient(es), n - 1, p, q);
+        const real* g = fgeo + ((size_t)side * 4) * n2 + mpq;
+        const real sc = es_slave(es) ? -g[3 * n2] : g[3 * n2];
+        const real nd[3] = {g[0] * sc, g[n2] * sc, g[2 * n2] * sc};
+        const real* b = sbuf + el2 * 15 * n3;
+        real kap = real(0);  // trace of the face's own lifting per unit jump
+#pragma unroll
+        for (int a = 0; a < n; ++a) kap += lw[a] * lv[a] * sSJ[el2 * n3 + vol_index(l, a, p, q, n)];
+        const real ek = ph.eta_br2 * kap;
+        real* own = LWf + ((size_t)(es_slave(es) * S + side) * NV) * n2 + mpq;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          real acc = real(0);
+#pragma unroll
+          for (int d = 0; d < 3; ++d) {
+            const int c = d * NV + v;
+            real lJ = ek * sF[((el2 * 6 + s) * 15 + c) * n2 + pq];
+#pragma unroll
+            for (int a = 0; a < n; ++a) lJ -= lv[a] * b[c * n3 + vol_index(l, a, p, q, n)];
+            acc += nd[d] * lJ;
+          }
+          sBr[((el2 * 6 + s) * NV + v) * n2 + pq] = acc;  // -> U* (both sides' mean)
+          own[v * n2] -= acc;                             // -> the element's own face state
+        }
+      }
     }
   }
   // reverse of a3: lam_lift = lamG / J ; W receives sum_d sum_l Ja^l_d (Dhat^T_l lam_lift^d)
@@ -639,6 +696,7 @@ __global__ void __launch_bounds__(Cfg<n>::T) k_adj_vol(
           for (int a = 0; a < n; ++a) sdv += lv[a] * b[(d * NV + v) * n3 + vol_index(l, a, p, q, n)];
           acc += nd[d] * sdv;
         }
+        if constexpr (BR2) acc += sBr[((el2 * 6 + s) * NV + v) * n2 + pq];
         dst[v * n2] = acc;
       }
     }
@@ -795,7 +853,11 @@ static cudaError_t rhs_adjoint_n(const DevMesh& m, const real* U, const real* la
   // forward recompute of face states, face gradients and volume gradients
   if ((err = prolong_n<real, n>(m, U, ops, ph, st)) != cudaSuccess) return err;
   if ((err = launch_bc<real>(m, t, ph, st)) != cudaSuccess) return err;
-  if ((err = lift_vol_n<real, n, 0>(m, U, ops, ph, 1, st)) != cudaSuccess) return err;
+  if (m.br2) {
+    if ((err = lift_vol_n<real, n, 0, false, 0, true>(m, U, ops, ph, 1, st)) != cudaSuccess) return err;
+  } else {
+    if ((err = lift_vol_n<real, n, 0>(m, U, ops, ph, 1, st)) != cudaSuccess) return err;
+  }
   k_adj_lamface<real, n><<<grid, C::T, 0, st>>>(lam, (const real*)m.sJ, m.elemSide, (real*)a.LF, m.K, m.S, ops);
   if (ph.riemann == 0 || ph.riemann == 2)
     k_adj_face<real, n, false><<<sgrid, 128, 0, st>>>((const real*)m.Wf, (const real*)m.Gf, (const real*)m.fgeo,
@@ -803,12 +865,21 @@ static cudaError_t rhs_adjoint_n(const DevMesh& m, const real* U, const real* la
   else
     k_adj_face<real, n, true><<<sgrid, 128, 0, st>>>((const real*)m.Wf, (const real*)m.Gf, (const real*)m.fgeo,
                                                      (const real*)a.LF, (real*)a.LWf, (real*)a.LGf, m.S, m.nBC, ph);
-  constexpr size_t smem = adj_vol_smem<real, n>();
-  static std::atomic<unsigned long long> attr{0};
-  if ((err = ensure_dynamic_smem(k_adj_vol<real, n>, smem, attr)) != cudaSuccess) return err;
-  k_adj_vol<real, n><<<grid, C::T, smem, st>>>(U, (const real*)m.Ja, (const real*)m.sJ, (const real*)m.Gvol,
-                                               (const real*)m.fgeo, m.elemSide, lam, (const real*)a.LGf,
-                                               (real*)a.LWs, (real*)a.muv, m.K, m.S, ops, ph);
+  if (m.br2) {
+    constexpr size_t smem = adj_vol_smem<real, n>(true);
+    static std::atomic<unsigned long long> attr{0};
+    if ((err = ensure_dynamic_smem(k_adj_vol<real, n, true>, smem, attr)) != cudaSuccess) return err;
+    k_adj_vol<real, n, true><<<grid, C::T, smem, st>>>(U, (const real*)m.Ja, (const real*)m.sJ, (const real*)m.Gvol,
+                                                       (const real*)m.fgeo, m.elemSide, lam, (const real*)a.LGf,
+                                                       (real*)a.LWs, (real*)a.LWf, (real*)a.muv, m.K, m.S, ops, ph);
+  } else {
+    constexpr size_t smem = adj_vol_smem<real, n>(false);
+    static std::atomic<unsigned long long> attr{0};
+    if ((err = ensure_dynamic_smem(k_adj_vol<real, n, false>, smem, attr)) != cudaSuccess) return err;
+    k_adj_vol<real, n, false><<<grid, C::T, smem, st>>>(U, (const real*)m.Ja, (const real*)m.sJ, (const real*)m.Gvol,
+                                                        (const real*)m.fgeo, m.elemSide, lam, (const real*)a.LGf,
+                                                        (real*)a.LWs, (real*)a.LWf, (real*)a.muv, m.K, m.S, ops, ph);
+  }
   k_adj_side<real, n><<<sgrid, 128, 0, st>>>((const real*)m.Wf, (const real*)a.LWs, (const real*)m.fgeo, m.bcKind,
                                              (real*)a.LWf, m.S, m.nBC, ph);
   k_adj_gather<real, n><<<grid, C::T, 0, st>>>((const real*)a.LWf, m.elemSide, (const real*)a.muv, out, scale,

@@ -1,7 +1,8 @@
 """Discrete adjoint of the CUDA path on meshes with boundaries (exact-state,
-outflow and slip-wall sides; the manufactured source term) and with the HLLC,
-Rusanov and entropy-conservative fluxes (reversed by dual numbers) against the
-oracle's reverse-mode derivative and central finite-difference dot-product tests."""
+outflow and slip-wall sides; the manufactured source term), with the HLLC,
+Rusanov and entropy-conservative fluxes (reversed by dual numbers) and with BR2
+face gradients, against the oracle's reverse-mode derivative and central
+finite-difference dot-product tests."""
 import numpy as np
 import pytest
 import torch
@@ -37,18 +38,22 @@ CASES = [
 ]
 
 
-def _pair(case):
+def _pair(case, eta=None):
+    """GPU solver and oracle for a case; eta given: BR2 lifting with that penalty."""
     from paper_1910_02858_gb300 import Solver, SolverConfig
 
     name, mk, N, nt, riem, bc_exact, source, kinds = case
     mk = dict(dict(lo=(-1,) * 3, hi=(1,) * 3, periodic=(False,) * 3), **mk)
     mesh = wl.box_mesh(**mk)
+    lift = {} if eta is None else dict(lifting=1, eta_br2=eta)
     s = Solver(SolverConfig(N=N, Ngeo=mk.get("Ngeo", 1), node_type=nt, riemann=riem, mu=1 / 400.0,
-                            bc_exact=bc_exact, source=source, adjoint=True), mesh.coords, mesh.conn, device=DEV)
+                            bc_exact=bc_exact, source=source, adjoint=True, **lift), mesh.coords, mesh.conn,
+               device=DEV)
     for bc_id, kind in kinds.items():
         s.set_bc(bc_id, kind)
+    olift = {} if eta is None else dict(lifting="br2", eta_br2=eta)
     dg = DGSEM(Params(N=N, node_type=nt, riemann=RIEM[riem], smooth_roe=riem == 2, mu=1 / 400.0, bc_exact=bc_exact,
-                      source=source, bc_kinds=dict(kinds)), mesh.coords, mesh.conn)
+                      source=source, bc_kinds=dict(kinds), **olift), mesh.coords, mesh.conn)
     U0 = wl.perturbed(np.pi * mesh.node_coords(N, nt), seed=7)
     return s, dg, U0
 
@@ -123,3 +128,48 @@ def test_adjoint_with_boundaries_fp32_vs_fp64():
     d = (a - b).transpose(0, 1).reshape(5, -1).norm(dim=1)
     r = a.transpose(0, 1).reshape(5, -1).norm(dim=1)
     assert float((d / r).max()) < 1e-4, (d / r).tolist()
+
+
+BR2_CASES = [  # (case, eta)
+    (CASES[0], 2.0), (CASES[1], 2.0), (CASES[2], 0.0), (CASES[4], 5.0), (CASES[6], 2.0),
+]
+
+
+@pytest.mark.parametrize("case,eta", BR2_CASES, ids=[f"br2_{c[0]}_eta{e:g}" for c, e in BR2_CASES])
+def test_rhs_adjoint_br2_vs_oracle(case, eta):
+    """BR2 face gradients (broken gradient plus eta times the face's own lifting):
+    the reverse of the jumps reaches U* and the element's own face state."""
+    s, dg, U0 = _pair(case, eta)
+    lam = np.random.default_rng(4).normal(size=U0.shape)
+    out = s.rhs_adjoint(torch.tensor(U0, device=DEV), torch.tensor(lam, device=DEV), 0.3)
+    ref = dg.rhs_vjp(torch.tensor(U0), 0.3, torch.tensor(lam))
+    s.close()
+    d = (out.cpu() - ref).transpose(0, 1).reshape(5, -1).norm(dim=1)
+    r = ref.transpose(0, 1).reshape(5, -1).norm(dim=1)
+    assert float((d / r).max()) < 1e-10, (d / r).tolist()
+
+
+def test_br2_adjoint_dot_product_and_step():
+    """BR2 without the oracle: central-difference dot-product test; and one reverse
+    LSERK4(5) step against the oracle."""
+    s, dg, U0 = _pair(CASES[0], 2.0)
+    Ud = torch.tensor(U0, device=DEV)
+    g = torch.Generator(device="cpu").manual_seed(6)
+    v = torch.randn(Ud.shape, generator=g, dtype=torch.float64).to(DEV)
+    lam = torch.randn(Ud.shape, generator=g, dtype=torch.float64).to(DEV)
+    eps = 1e-6
+    Jv = (s.rhs(Ud + eps * v, 0.1) - s.rhs(Ud - eps * v, 0.1)) / (2 * eps)
+    a = float((lam * Jv).sum())
+    b = float((s.rhs_adjoint(Ud, lam, 0.1) * v).sum())
+    assert abs(a - b) < 1e-6 * abs(b), (a, b)
+    rng = np.random.default_rng(11)
+    lamU0, lamdU0 = rng.normal(size=U0.shape), rng.normal(size=U0.shape)
+    stages = torch.empty((5,) + Ud.shape, dtype=Ud.dtype, device=DEV)
+    s.step_stages(Ud.clone(), torch.zeros_like(Ud), 0.2, 1e-3, stages)
+    lamU, lamdU = torch.tensor(lamU0, device=DEV), torch.tensor(lamdU0, device=DEV)
+    s.adjoint_step(stages, lamU, lamdU, 0.2, 1e-3)
+    st_ref = []
+    dg.rk_step(torch.tensor(U0), torch.zeros_like(torch.tensor(U0)), 0.2, 1e-3, stages_out=st_ref)
+    rU, _ = dg.adjoint_step(st_ref, torch.tensor(lamU0), torch.tensor(lamdU0), 0.2, 1e-3)
+    s.close()
+    assert float((lamU.cpu() - rU).norm() / rU.norm()) < 1e-12
