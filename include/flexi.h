@@ -181,8 +181,8 @@ flexi_status flexi_rk_step_stages(flexi_ctx *ctx, void *U, void *dU, double t, d
  * U_stages: device [5][K][5][n^3] as written by flexi_rk_step_stages; t: the
  * step's start time (exact-state boundaries are evaluated at the stage times of
  * the forward step).  lamU, lam_dU: device, updated in place.  Requires
- * flexi_params.adjoint = 1, FLEXI_FP64 or FLEXI_FP32, BR1 or BR2 lifting and
- * the standard volume integral; every numerical flux (the Roe fluxes by a
+ * flexi_params.adjoint = 1, FLEXI_FP64 or FLEXI_FP32, BR1 or BR2 lifting, the
+ * standard or the split-form volume integral; every numerical flux (the Roe fluxes by a
  * hand-written reverse, HLLC, Rusanov and EC in forward mode); periodic meshes
  * and meshes with boundaries of every kind (the outer state's dependence on the
  * inner one is transposed; a source term does not depend on U); no mortars

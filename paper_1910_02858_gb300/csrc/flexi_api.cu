@@ -771,7 +771,7 @@ flexi_status flexi_rk_step_stages(flexi_ctx* c, void* U, void* dU, double t, dou
 }
 
 static bool adjoint_supported(const flexi_ctx* c) {
-  return c->p.adjoint && c->nMortar == 0 && c->p.split_form == FLEXI_SPLIT_STANDARD;
+  return c->p.adjoint && c->nMortar == 0;
 }
 
 flexi_status flexi_adjoint_step(flexi_ctx* c, const void* U_stages, void* lamU, void* lam_dU, double t, double dt,

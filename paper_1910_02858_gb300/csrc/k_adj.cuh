@@ -1,7 +1,7 @@
 // Discrete adjoint of the right-hand side: mu = (dL/dU)^T lam, by hand-written
 // reverse mode of every step of the forward operator (steps a1..a9 of k_dg.cuh),
-// for BR1 or BR2 lifting and the standard volume integral, on periodic meshes and
-// meshes with boundary sides.  Numerical flux: the Roe fluxes have a hand-written
+// for BR1 or BR2 lifting and the standard or split-form volume integral, on
+// periodic meshes and meshes with boundary sides.  Numerical flux: the Roe fluxes have a hand-written
 // reverse; HLLC, Rusanov and the entropy-conservative flux are differentiated in
 // forward mode (dual numbers, ten tangents per face node).
 // Boundary sides: the outer state is a function of the inner one (outflow: the
@@ -366,6 +366,60 @@ __device__ void riemann_vjp_dual(const real WL[NV], const real WR[NV], const rea
   }
 }
 
+// 2 F#(W_x, W_a) in the direction of the pair's metric terms (Eq. semiDiscreteSplit):
+// SPLIT 1 Pirozzoli's kinetic-energy-preserving flux with Jx + Ja (the form the
+// forward kernel accumulates, D times this), SPLIT 2 twice Chandrashekar's
+// entropy-conservative flux with (Jx + Ja)/2.  T is the arithmetic or a dual number.
+template <typename T, int SPLIT>
+__device__ __forceinline__ void split_pair_flux(const T Wx[NV], const T Wa[NV], const T Jx[3], const T Ja[3],
+                                                const Phys<T>& ph, T F[NV]) {
+  if constexpr (SPLIT == 2) {
+    const T ux[3] = {Wx[1], Wx[2], Wx[3]}, ua[3] = {Wa[1], Wa[2], Wa[3]};
+    const T Jm[3] = {T(0.5) * (Jx[0] + Ja[0]), T(0.5) * (Jx[1] + Ja[1]), T(0.5) * (Jx[2] + Ja[2])};
+    ec_flux(Wx[0], ux, T(0.5) * Wx[0] / Wx[4], ux[0] * ux[0] + ux[1] * ux[1] + ux[2] * ux[2], Wa[0], ua,
+            T(0.5) * Wa[0] / Wa[4], ua[0] * ua[0] + ua[1] * ua[1] + ua[2] * ua[2], Jm, ph, F);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) F[v] = T(2) * F[v];
+  } else {
+    const T Hx = (Wx[4] * ph.inv_gm1 + T(0.5) * Wx[0] * (Wx[1] * Wx[1] + Wx[2] * Wx[2] + Wx[3] * Wx[3]) + Wx[4]) / Wx[0];
+    const T Ha = (Wa[4] * ph.inv_gm1 + T(0.5) * Wa[0] * (Wa[1] * Wa[1] + Wa[2] * Wa[2] + Wa[3] * Wa[3]) + Wa[4]) / Wa[0];
+    const T rs = Wx[0] + Wa[0], us = Wx[1] + Wa[1], vs = Wx[2] + Wa[2], ws = Wx[3] + Wa[3];
+    const T ps = Wx[4] + Wa[4], Hs = Hx + Ha;
+    const T j0 = Jx[0] + Ja[0], j1 = Jx[1] + Ja[1], j2 = Jx[2] + Ja[2];
+    const T m = T(0.125) * rs * (us * j0 + vs * j1 + ws * j2);
+    const T hp = T(0.5) * ps;
+    F[0] = T(2) * m;
+    F[1] = m * us + hp * j0;
+    F[2] = m * vs + hp * j1;
+    F[3] = m * ws + hp * j2;
+    F[4] = m * Hs;
+  }
+}
+
+// lamWx += d/dW_x (w . 2F#(W_x, W_a)); both = true: W_a is W_x (the diagonal pair)
+template <typename real, int SPLIT>
+__device__ __forceinline__ void split_pair_vjp(const real Wx[NV], const real Wa[NV], const real Jx[3],
+                                               const real Ja[3], const Phys<Dual<real>>& pd, const real w[NV],
+                                               bool both, real lamWx[NV]) {
+  using D = Dual<real>;
+  const D jx[3] = {D(Jx[0], real(0)), D(Jx[1], real(0)), D(Jx[2], real(0))};
+  const D ja[3] = {D(Ja[0], real(0)), D(Ja[1], real(0)), D(Ja[2], real(0))};
+#pragma unroll 1
+  for (int c = 0; c < NV; ++c) {
+    D x[NV], a[NV], F[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      x[v] = D(Wx[v], v == c ? real(1) : real(0));
+      a[v] = D(Wa[v], (both && v == c) ? real(1) : real(0));
+    }
+    split_pair_flux<D, SPLIT>(x, a, jx, ja, pd, F);
+    real sdot = real(0);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) sdot += w[v] * F[v].d;
+    lamWx[c] += sdot;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // kernels
 // ---------------------------------------------------------------------------
@@ -495,10 +549,11 @@ __device__ __forceinline__ real dhatT_line(const real* __restrict__ sD, const re
 }
 
 template <typename real, int n>
-constexpr size_t adj_vol_smem(bool br2) {
+constexpr size_t adj_vol_smem(bool br2, bool split) {
   using C = Cfg<n>;
   return sizeof(real) * (C::NE * 15 * C::n3 + C::NE * 6 * 15 * C::n2 + C::n2 + 4 * n +
-                         (br2 ? C::NE * C::n3 + C::NE * 6 * NV * C::n2 : 0)) +
+                         (br2 ? C::NE * C::n3 + C::NE * 6 * NV * C::n2 : 0) +
+                         (split ? C::n2 + C::NE * 14 * C::n3 : 0)) +
          sizeof(int) * C::NE * 8;
 }
 
@@ -506,7 +561,11 @@ constexpr size_t adj_vol_smem(bool br2) {
 // the face's own lifting, r_f = (1/J) l_hat_f Jm_f with the jump
 // Jm_f = (U* - W_own) n s_hat; their adjoints reach U* (added to LWs) and the
 // element's own face state (added to its slot of LWf, written by k_adj_face).
-template <typename real, int n, bool BR2>
+// SPLIT (Gauss-Lobatto): the reverse of the split-form volume integral: the viscous
+// part as in the standard form, the two-point advective sums by dual numbers per
+// pair (each node collects d/dW of both ordered pairs it takes part in) and the
+// strong-form face terms at the line ends.
+template <typename real, int n, bool BR2, int SPLIT>
 __global__ void __launch_bounds__(Cfg<n>::T) k_adj_vol(
     const real* __restrict__ U, const real* __restrict__ Ja, const real* __restrict__ sJ, const real* __restrict__ Gvol,
     const real* __restrict__ fgeo, const int* __restrict__ elemSide, const real* __restrict__ lam,
@@ -520,7 +579,9 @@ __global__ void __launch_bounds__(Cfg<n>::T) k_adj_vol(
   real* sOp = sF + NE * 6 * 15 * n2;
   real* sSJ = sOp + n2 + 4 * n;                 // BR2: [NE][n3] 1/J
   real* sBr = sSJ + (BR2 ? NE * n3 : 0);        // BR2: [NE][6][5][n2] adjoint of U* from the jumps
-  int* sES = reinterpret_cast<int*>(sBr + (BR2 ? NE * 6 * NV * n2 : 0));
+  real* sDT = sBr + (BR2 ? NE * 6 * NV * n2 : 0);  // SPLIT: DT[a * n + i] = D[i][a]
+  real* sWJ = sDT + (SPLIT ? n2 : 0);              // SPLIT: [NE][14][n3] W (5) and Ja (9) per node
+  int* sES = reinterpret_cast<int*>(sWJ + (SPLIT ? NE * 14 * n3 : 0));
   const int tid = threadIdx.x;
   const int el = tid / n3, node = tid - el * n3;
   const int e0 = blockIdx.x * NE;
@@ -551,6 +612,14 @@ __global__ void __launch_bounds__(Cfg<n>::T) k_adj_vol(
   // lam_vol = -lam / J into the buffer
 #pragma unroll
   for (int v = 0; v < NV; ++v) myb[v * n3 + node] = valid ? -lam[((size_t)e * NV + v) * n3 + node] * sj : real(0);
+  if constexpr (SPLIT) {
+    for (int t = tid; t < n2; t += T) sDT[t] = ops.DT[t];
+    real* wj = sWJ + el * 14 * n3 + node;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) wj[v * n3] = W[v];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) wj[(NV + c) * n3] = jac[c];
+  }
   // face-gradient adjoints of the element's six faces (own slot)
   __syncthreads();
   for (int it = tid; it < NE * 6 * n2; it += T) {
@@ -586,9 +655,50 @@ __global__ void __launch_bounds__(Cfg<n>::T) k_adj_vol(
         ld[v] = jac[0 * 3 + d] * lFl[0][v] + jac[1 * 3 + d] * lFl[1][v] + jac[2 * 3 + d] * lFl[2][v];
         lvisc[d][v] = -ld[v];
       }
-      conv_vjp(Uo, W, d, ld, lamU, lamW);
+      if constexpr (!SPLIT) conv_vjp(Uo, W, d, ld, lamU, lamW);
     }
     visc_vjp(W, G, lvisc, ph, lamW, lamG);
+  }
+  if constexpr (SPLIT) {
+    // advective part: sum_l sum_a D_{i_l a} 2F#(x, a) at every node x; node x collects
+    // d/dW_x of its own sums (weight D[i_x][a] lam_x) and of its partners' sums in
+    // which it appears (weight D[a][i_x] lam_a), in one evaluation per partner
+    const Phys<Dual<real>> pd = dual_phys(ph);
+    const real* lv = myb;  // lam_vol [5][n3] of this element
+    const real* wj = sWJ + el * 14 * n3;
+#pragma unroll 1
+    for (int l = 0; l < 3; ++l) {
+      const int ix = l == 0 ? i : (l == 1 ? j : k);
+      const real Jx[3] = {jac[l * 3], jac[l * 3 + 1], jac[l * 3 + 2]};
+      real lx[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) lx[v] = lv[v * n3 + node];
+#pragma unroll 1
+      for (int a = 0; a < n; ++a) {
+        const int na = l == 0 ? a + n * (j + n * k) : (l == 1 ? i + n * (a + n * k) : i + n * (j + n * a));
+        real Wa[NV], w[NV];
+        const real Jpa[3] = {wj[(NV + 3 * l) * n3 + na], wj[(NV + 3 * l + 1) * n3 + na],
+                             wj[(NV + 3 * l + 2) * n3 + na]};
+        const real dxa = sDT[a * n + ix], dax = sDT[ix * n + a];  // D[ix][a], D[a][ix]
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          Wa[v] = wj[v * n3 + na];
+          w[v] = a == ix ? dxa * lx[v] : dxa * lx[v] + dax * lv[v * n3 + na];
+        }
+        split_pair_vjp<real, SPLIT>(W, Wa, Jx, Jpa, pd, w, a == ix, lamW);
+      }
+      // strong-form face terms at the line ends: c Fcal^{c,l}(U_x)
+      if (ix == 0 || ix == n - 1) {
+        const real c = ix == 0 ? sOp[n2 + 2 * n] : -sOp[n2 + 3 * n + n - 1];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          real lf[NV];
+#pragma unroll
+          for (int v = 0; v < NV; ++v) lf[v] = c * Jx[d] * lx[v];
+          conv_vjp(Uo, W, d, lf, lamU, lamW);
+        }
+      }
+    }
   }
   // reverse of a4: face gradients = prolongation of G
   {
@@ -841,6 +951,19 @@ inline AdjScratch adj_layout(const DevMesh& m, void* base, size_t rs) {
   return a;
 }
 
+template <typename real, int n, bool BR2, int SPLIT>
+static cudaError_t launch_adj_vol(const DevMesh& m, const real* U, const real* lam, const AdjScratch& a,
+                                  const Ops<real>& ops, const Phys<real>& ph, int grid, cudaStream_t st) {
+  constexpr size_t smem = adj_vol_smem<real, n>(BR2, SPLIT != 0);
+  static std::atomic<unsigned long long> attr{0};
+  cudaError_t err = ensure_dynamic_smem(k_adj_vol<real, n, BR2, SPLIT>, smem, attr);
+  if (err != cudaSuccess) return err;
+  k_adj_vol<real, n, BR2, SPLIT><<<grid, Cfg<n>::T, smem, st>>>(
+      U, (const real*)m.Ja, (const real*)m.sJ, (const real*)m.Gvol, (const real*)m.fgeo, m.elemSide, lam,
+      (const real*)a.LGf, (real*)a.LWs, (real*)a.LWf, (real*)a.muv, m.K, m.S, ops, ph);
+  return cudaGetLastError();
+}
+
 template <typename real, int n>
 static cudaError_t rhs_adjoint_n(const DevMesh& m, const real* U, const real* lam, real* out, real scale,
                                  int accumulate, const Ops<real>& ops, const Phys<real>& ph, void* scratch, double t,
@@ -866,19 +989,13 @@ static cudaError_t rhs_adjoint_n(const DevMesh& m, const real* U, const real* la
     k_adj_face<real, n, true><<<sgrid, 128, 0, st>>>((const real*)m.Wf, (const real*)m.Gf, (const real*)m.fgeo,
                                                      (const real*)a.LF, (real*)a.LWf, (real*)a.LGf, m.S, m.nBC, ph);
   if (m.br2) {
-    constexpr size_t smem = adj_vol_smem<real, n>(true);
-    static std::atomic<unsigned long long> attr{0};
-    if ((err = ensure_dynamic_smem(k_adj_vol<real, n, true>, smem, attr)) != cudaSuccess) return err;
-    k_adj_vol<real, n, true><<<grid, C::T, smem, st>>>(U, (const real*)m.Ja, (const real*)m.sJ, (const real*)m.Gvol,
-                                                       (const real*)m.fgeo, m.elemSide, lam, (const real*)a.LGf,
-                                                       (real*)a.LWs, (real*)a.LWf, (real*)a.muv, m.K, m.S, ops, ph);
+    if ((err = launch_adj_vol<real, n, true, 0>(m, U, lam, a, ops, ph, grid, st)) != cudaSuccess) return err;
+  } else if (m.split == 1) {
+    if ((err = launch_adj_vol<real, n, false, 1>(m, U, lam, a, ops, ph, grid, st)) != cudaSuccess) return err;
+  } else if (m.split == 2) {
+    if ((err = launch_adj_vol<real, n, false, 2>(m, U, lam, a, ops, ph, grid, st)) != cudaSuccess) return err;
   } else {
-    constexpr size_t smem = adj_vol_smem<real, n>(false);
-    static std::atomic<unsigned long long> attr{0};
-    if ((err = ensure_dynamic_smem(k_adj_vol<real, n, false>, smem, attr)) != cudaSuccess) return err;
-    k_adj_vol<real, n, false><<<grid, C::T, smem, st>>>(U, (const real*)m.Ja, (const real*)m.sJ, (const real*)m.Gvol,
-                                                        (const real*)m.fgeo, m.elemSide, lam, (const real*)a.LGf,
-                                                        (real*)a.LWs, (real*)a.LWf, (real*)a.muv, m.K, m.S, ops, ph);
+    if ((err = launch_adj_vol<real, n, false, 0>(m, U, lam, a, ops, ph, grid, st)) != cudaSuccess) return err;
   }
   k_adj_side<real, n><<<sgrid, 128, 0, st>>>((const real*)m.Wf, (const real*)a.LWs, (const real*)m.fgeo, m.bcKind,
                                              (real*)a.LWf, m.S, m.nBC, ph);

@@ -1,8 +1,9 @@
 """Discrete adjoint of the CUDA path on meshes with boundaries (exact-state,
 outflow and slip-wall sides; the manufactured source term), with the HLLC,
 Rusanov and entropy-conservative fluxes (reversed by dual numbers) and with BR2
-face gradients, against the oracle's reverse-mode derivative and central
-finite-difference dot-product tests."""
+face gradients or the split-form volume integral (KEP / EC two-point fluxes),
+against the oracle's reverse-mode derivative and central finite-difference
+dot-product tests."""
 import numpy as np
 import pytest
 import torch
@@ -38,20 +39,25 @@ CASES = [
 ]
 
 
-def _pair(case, eta=None):
-    """GPU solver and oracle for a case; eta given: BR2 lifting with that penalty."""
+def _pair(case, eta=None, split=0):
+    """GPU solver and oracle for a case; eta given: BR2 lifting with that penalty;
+    split 1 / 2: the kinetic-energy-preserving / entropy-conservative split form."""
     from paper_1910_02858_gb300 import Solver, SolverConfig
 
     name, mk, N, nt, riem, bc_exact, source, kinds = case
     mk = dict(dict(lo=(-1,) * 3, hi=(1,) * 3, periodic=(False,) * 3), **mk)
     mesh = wl.box_mesh(**mk)
     lift = {} if eta is None else dict(lifting=1, eta_br2=eta)
+    if split:
+        lift["split_form"] = split
     s = Solver(SolverConfig(N=N, Ngeo=mk.get("Ngeo", 1), node_type=nt, riemann=riem, mu=1 / 400.0,
                             bc_exact=bc_exact, source=source, adjoint=True, **lift), mesh.coords, mesh.conn,
                device=DEV)
     for bc_id, kind in kinds.items():
         s.set_bc(bc_id, kind)
     olift = {} if eta is None else dict(lifting="br2", eta_br2=eta)
+    if split:
+        olift["split"] = {1: "pirozzoli", 2: "chandrashekar"}[split]
     dg = DGSEM(Params(N=N, node_type=nt, riemann=RIEM[riem], smooth_roe=riem == 2, mu=1 / 400.0, bc_exact=bc_exact,
                       source=source, bc_kinds=dict(kinds), **olift), mesh.coords, mesh.conn)
     U0 = wl.perturbed(np.pi * mesh.node_coords(N, nt), seed=7)
@@ -173,3 +179,40 @@ def test_br2_adjoint_dot_product_and_step():
     rU, _ = dg.adjoint_step(st_ref, torch.tensor(lamU0), torch.tensor(lamdU0), 0.2, 1e-3)
     s.close()
     assert float((lamU.cpu() - rU).norm() / rU.norm()) < 1e-12
+
+
+SPLIT_CASES = [  # Gauss-Lobatto cases (the split form is built on LGL nodes) x split form
+    (CASES[1], 1), (CASES[1], 2), (CASES[6], 1), (CASES[7], 2),
+    (("kep_periodic_lgl_N4_hllc", dict(nelem=(2, 3, 2), periodic=(True,) * 3, reorient_seed=8), 4, 1, 1, 1, False,
+      {}), 1),
+    (("kep_curved_lgl_N3_roe_bc", dict(nelem=(2, 2, 3), Ngeo=3, mapping="sine", reorient_seed=9,
+                                       bc_ids=[0, 1, 2, 2, 1, 0]), 3, 1, 2, 1, False, {1: 1, 2: 2}), 1),
+]
+
+
+@pytest.mark.parametrize("case,split", SPLIT_CASES, ids=[f"split{sp}_{c[0]}" for c, sp in SPLIT_CASES])
+def test_rhs_adjoint_split_form_vs_oracle(case, split):
+    s, dg, U0 = _pair(case, split=split)
+    lam = np.random.default_rng(5).normal(size=U0.shape)
+    out = s.rhs_adjoint(torch.tensor(U0, device=DEV), torch.tensor(lam, device=DEV), 0.3)
+    ref = dg.rhs_vjp(torch.tensor(U0), 0.3, torch.tensor(lam))
+    s.close()
+    d = (out.cpu() - ref).transpose(0, 1).reshape(5, -1).norm(dim=1)
+    r = ref.transpose(0, 1).reshape(5, -1).norm(dim=1)
+    assert float((d / r).max()) < 1e-10, (d / r).tolist()
+
+
+@pytest.mark.parametrize("split", [1, 2])
+def test_split_form_adjoint_dot_product(split):
+    """Central-difference dot-product test of the split-form adjoint (no oracle)."""
+    s, _, U0 = _pair(CASES[1], split=split)
+    Ud = torch.tensor(U0, device=DEV)
+    g = torch.Generator(device="cpu").manual_seed(7)
+    v = torch.randn(Ud.shape, generator=g, dtype=torch.float64).to(DEV)
+    lam = torch.randn(Ud.shape, generator=g, dtype=torch.float64).to(DEV)
+    eps = 1e-6
+    Jv = (s.rhs(Ud + eps * v, 0.1) - s.rhs(Ud - eps * v, 0.1)) / (2 * eps)
+    a = float((lam * Jv).sum())
+    b = float((s.rhs_adjoint(Ud, lam, 0.1) * v).sum())
+    s.close()
+    assert abs(a - b) < 1e-6 * abs(b), (a, b)

@@ -157,14 +157,14 @@ def test_split_unsupported_combinations():
     with pytest.raises(F.FlexiError) as ei:
         _solver(dict(N=3, node_type=1, riemann=5), mesh)
     assert ei.value.code == F.FLEXI_EINVAL
+    # the split-form adjoint runs (its parity with the oracle: test_gpu_adjoint_bc.py)
     s = _solver(dict(N=3, node_type=1, split_form=KEP, riemann=0, adjoint=True), mesh)
     U = torch.tensor(wl.taylor_green(mesh.node_coords(3, 1)), device=DEV)
     lam = torch.ones_like(U)
     out = torch.empty_like(U)
-    with pytest.raises(F.FlexiError) as ei:
-        F.flexi_rhs_adjoint(s.ctx, U, lam, out, 0.0, torch.cuda.current_stream())
+    F.flexi_rhs_adjoint(s.ctx, U, lam, out, 0.0, torch.cuda.current_stream())
     s.close()
-    assert ei.value.code == F.FLEXI_EUNSUPPORTED
+    assert bool(torch.isfinite(out).all())
 
 
 
