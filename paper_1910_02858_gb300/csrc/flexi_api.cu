@@ -591,8 +591,8 @@ template <typename real>
 flexi_status do_rhs_adjoint(flexi_ctx* c, const real* U, const real* lam, real* out, real scale, int accumulate,
                             double t, cudaStream_t st) {
   Prof pr(c, KC_ADJ, st);
-  CK(launch_rhs_adjoint<real>(c->m, U, lam, out, scale, accumulate, ops_of<real>(c), ph_of<real>(c), c->adj_scratch,
-                              t, st));
+  CK(launch_rhs_adjoint<real>(c->m, U, lam, out, scale, accumulate, ops_of<real>(c), mo_of<real>(c), ph_of<real>(c),
+                              c->adj_scratch, t, st));
   return FLEXI_OK;
 }
 
@@ -661,7 +661,8 @@ bool ctx_reduce_inputs(const flexi_ctx* c, ReduceInputs* r) {
 
 size_t adjoint_scratch_bytes(const DevMesh& m, size_t rs) {
   const size_t n2 = (size_t)m.n * m.n, n3 = n2 * m.n;
-  return rs * (4 * 2 * (size_t)m.S * NV * n2 + 2 * (size_t)m.S * 15 * n2 + (size_t)m.K * NV * n3);
+  return rs * (4 * 2 * (size_t)m.S * NV * n2 + 2 * (size_t)m.S * 15 * n2 + (size_t)m.K * NV * n3 +
+               (size_t)m.nBig * 15 * n2);
 }
 }  // namespace flexi
 
@@ -771,7 +772,7 @@ flexi_status flexi_rk_step_stages(flexi_ctx* c, void* U, void* dU, double t, dou
 }
 
 static bool adjoint_supported(const flexi_ctx* c) {
-  return c->p.adjoint && c->nMortar == 0;
+  return c->p.adjoint && (c->nMortar == 0 || c->p.lifting == FLEXI_LIFTING_BR1);
 }
 
 flexi_status flexi_adjoint_step(flexi_ctx* c, const void* U_stages, void* lamU, void* lam_dU, double t, double dt,

@@ -1,7 +1,10 @@
 // Discrete adjoint of the right-hand side: mu = (dL/dU)^T lam, by hand-written
 // reverse mode of every step of the forward operator (steps a1..a9 of k_dg.cuh),
 // for BR1 or BR2 lifting and the standard or split-form volume integral, on
-// periodic meshes and meshes with boundary sides.  Numerical flux: the Roe fluxes have a hand-written
+// periodic meshes, meshes with boundary sides and (BR1) mortar meshes: the
+// interpolation of the big side's state and gradients and the projections of the
+// lifting and numerical fluxes are linear and are transposed in place
+// (k_adj_mortar_interp, k_adj_mortar_project).  Numerical flux: the Roe fluxes have a hand-written
 // reverse; HLLC, Rusanov and the entropy-conservative flux are differentiated in
 // forward mode (dual numbers, ten tangents per face node).
 // Boundary sides: the outer state is a function of the inner one (outflow: the
@@ -27,6 +30,7 @@
 #pragma once
 #include "dg_common.cuh"
 #include "k_dg.cuh"
+#include "k_mortar.cuh"
 #include "launch.h"
 
 namespace flexi {
@@ -473,10 +477,10 @@ template <typename real, int n, bool DUAL>
 __global__ void __launch_bounds__(128) k_adj_face(const real* __restrict__ Wf, const real* __restrict__ Gf,
                                                   const real* __restrict__ fgeo, const real* __restrict__ LF,
                                                   real* __restrict__ LWf, real* __restrict__ LGf, int S, int nBC,
-                                                  Phys<real> ph) {
+                                                  int nFace, Phys<real> ph) {
   constexpr int n2 = n * n;
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= S * n2) return;
+  if (idx >= nFace * n2) return;  // sides 0 .. nFace-1 carry a numerical flux (not the big sides of mortars)
   const int side = idx / n2, pq = idx - side * n2;
   const bool bnd = side < nBC;  // boundary side: no slave element, outer gradient = inner gradient
   real WL[NV], WR[NV], GL[15], GR[15], nv[3], lf[NV];
@@ -570,7 +574,7 @@ __global__ void __launch_bounds__(Cfg<n>::T) k_adj_vol(
     const real* __restrict__ U, const real* __restrict__ Ja, const real* __restrict__ sJ, const real* __restrict__ Gvol,
     const real* __restrict__ fgeo, const int* __restrict__ elemSide, const real* __restrict__ lam,
     const real* __restrict__ LGf, real* __restrict__ LWs, real* __restrict__ LWf, real* __restrict__ muv, int K, int S,
-    Ops<real> ops, Phys<real> ph) {
+    int bigBase, real* __restrict__ LQB, Ops<real> ops, Phys<real> ph) {
   using C = Cfg<n>;
   constexpr int n2 = C::n2, n3 = C::n3, NE = C::NE, T = C::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -807,7 +811,19 @@ __global__ void __launch_bounds__(Cfg<n>::T) k_adj_vol(
           acc += nd[d] * sdv;
         }
         if constexpr (BR2) acc += sBr[((el2 * 6 + s) * NV + v) * n2 + pq];
-        dst[v * n2] = acc;
+        dst[v * n2] = side >= bigBase ? real(0) : acc;  // big side: the lifting flux came from QB
+      }
+      if (side >= bigBase) {  // adjoint of the projected lifting flux QB (component v*3 + d)
+        real* lq = LQB + ((size_t)(side - bigBase) * 15) * n2 + mpq;
+#pragma unroll
+        for (int v = 0; v < NV; ++v)
+#pragma unroll
+          for (int d = 0; d < 3; ++d) {
+            real sdv = real(0);
+#pragma unroll
+            for (int a = 0; a < n; ++a) sdv += lv[a] * b[(d * NV + v) * n3 + vol_index(l, a, p, q, n)];
+            lq[(v * 3 + d) * n2] = sdv;
+          }
       }
     }
   }
@@ -827,11 +843,19 @@ __global__ void __launch_bounds__(Cfg<n>::T) k_adj_vol(
 template <typename real, int n>
 __global__ void __launch_bounds__(128) k_adj_side(const real* __restrict__ Wf, const real* __restrict__ LWs,
                                                   const real* __restrict__ fgeo, const int* __restrict__ bcKind,
-                                                  real* __restrict__ LWf, int S, int nBC, Phys<real> ph) {
+                                                  real* __restrict__ LWf, int S, int nBC, int bigBase, Phys<real> ph) {
   constexpr int n2 = n * n;
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= S * n2) return;
   const int side = idx / n2, pq = idx - side * n2;
+  if (side >= bigBase) {  // big side of a mortar: its state reaches the flux only through the
+#pragma unroll            // interpolation, whose transpose k_adj_mortar_interp adds afterwards
+    for (int v = 0; v < NV; ++v) {
+      LWf[((size_t)side * NV + v) * n2 + pq] = real(0);
+      LWf[((size_t)(S + side) * NV + v) * n2 + pq] = real(0);
+    }
+    return;
+  }
   if (side < nBC) {
     real W[NV], lW[NV], lWR[NV], lU[NV] = {0, 0, 0, 0, 0};
 #pragma unroll
@@ -933,10 +957,172 @@ __global__ void k_axpby(real* __restrict__ y, const real* __restrict__ x, real a
 }
 
 // ---------------------------------------------------------------------------
+// mortars: transposes of the interpolation and the projections (k_mortar.cuh)
+// ---------------------------------------------------------------------------
+// Transpose of k_mortar_interp: the adjoints of the virtual sides' slot 1 (NC
+// components in each virtual side's frame) are mapped into the sub-square frame,
+// multiplied by I^T along q and along p, and summed into the big side's slot 0
+// (ACC: added to it, else written).  NC = 15: face gradients; NC = 5: conservative
+// face states (the forward interpolates U = cons(W) and converts back, so the
+// composition with the big side's primitive state is the identity).
+template <typename real, int n, int NC, bool ACC>
+__global__ void __launch_bounds__(kMortarThreads) k_adj_mortar_interp(real* __restrict__ L, const int* __restrict__ mbig,
+                                                                      const int4* __restrict__ mvirt, int S,
+                                                                      int bigBase, int vbase, MortarOps<real> mo) {
+  constexpr int n2 = n * n;
+  constexpr int PT = (n2 + kMortarThreads - 1) / kMortarThreads;
+  __shared__ real sY[NC * n2];
+  __shared__ real sT[NC * n2];
+  const int tid = threadIdx.x;
+  const int bi = blockIdx.x;
+  const int* mb = mbig + bi * 8;
+  const int typ = mb[0];
+  real acc[PT][NC];
+#pragma unroll
+  for (int k = 0; k < PT; ++k)
+#pragma unroll
+    for (int c = 0; c < NC; ++c) acc[k][c] = real(0);
+  for (int pos = 0; pos < 4; ++pos) {
+    const int v = mb[1 + pos];
+    if (v < 0) continue;  // uniform across the CTA
+    int a, b;
+    mortar_ab(typ, pos, a, b);
+    const int oinv = mvirt[v - vbase].w;
+    for (int t = tid; t < n2; t += kMortarThreads) {  // sub node (pp, qq) of virtual node T_oinv(pp, qq)
+      const real* src = L + ((size_t)(S + v) * NC) * n2 + orient_pq(oinv, n - 1, t % n, t / n);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) sY[c * n2 + t] = src[c * n2];
+    }
+    __syncthreads();
+    // transpose of the pass along q: sT[m][pp] = sum_qq I^b[qq][m] sY[qq][pp]
+    for (int t = tid; t < n2; t += kMortarThreads) {
+      const int m = t / n, pp = t - m * n;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        real y;
+        if (typ & 2) {
+          y = real(0);
+#pragma unroll
+          for (int qq = 0; qq < n; ++qq) y += mo.I[b][qq * n + m] * sY[c * n2 + qq * n + pp];
+        } else {
+          y = sY[c * n2 + t];
+        }
+        sT[c * n2 + t] = y;
+      }
+    }
+    __syncthreads();
+    // transpose of the pass along p: big node (m, q) += sum_p' I^a[p'][m] sT[q][p']
+#pragma unroll
+    for (int k = 0; k < PT; ++k) {
+      const int t = tid + k * kMortarThreads;
+      if (t < n2) {
+        const int q = t / n, m = t - q * n;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          if (typ & 1) {
+#pragma unroll
+            for (int pp = 0; pp < n; ++pp) acc[k][c] += mo.I[a][pp * n + m] * sT[c * n2 + q * n + pp];
+          } else {
+            acc[k][c] += sT[c * n2 + t];
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int k = 0; k < PT; ++k) {
+    const int t = tid + k * kMortarThreads;
+    if (t < n2) {
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        real* dst = L + ((size_t)(bigBase + bi) * NC + c) * n2 + t;
+        *dst = ACC ? *dst + acc[k][c] : acc[k][c];
+      }
+    }
+  }
+}
+
+// Transpose of k_mortar_project: y = (P^a)^T (P^b)^T of the big side's adjoint,
+// mapped to each virtual side's own node.  KIND 1 (numerical flux): written to
+// slot 1 of the virtual side's LF, so that k_adj_face's slot difference
+// LF0 - LF1 applies the projection's minus sign.  KIND 0 (BR1 lifting flux of the
+// big element, from LQB): adjoint of U* of the virtual side, -s_hat sum_d n_d
+// y_{v*3+d}, written to slot 1 of LWs (k_adj_side adds half of it to each slot).
+template <typename real, int n, int KIND>
+__global__ void __launch_bounds__(kMortarThreads) k_adj_mortar_project(
+    const real* __restrict__ Lbig, real* __restrict__ Lv, const real* __restrict__ fgeo, const int* __restrict__ mbig,
+    const int4* __restrict__ mvirt, int S, int bigBase, int vbase, MortarOps<real> mo) {
+  constexpr int n2 = n * n;
+  constexpr int NC = KIND == 0 ? 15 : NV;
+  __shared__ real sB[NC * n2];
+  __shared__ real sT[NC * n2];
+  const int tid = threadIdx.x;
+  const int bi = blockIdx.x;
+  const int* mb = mbig + bi * 8;
+  const int typ = mb[0];
+  const real* src = Lbig + (KIND == 0 ? (size_t)bi * 15 * n2 : (size_t)(bigBase + bi) * NV * n2);
+  for (int t = tid; t < NC * n2; t += kMortarThreads) sB[t] = src[t];
+  __syncthreads();
+  for (int pos = 0; pos < 4; ++pos) {
+    const int v = mb[1 + pos];
+    if (v < 0) continue;  // uniform across the CTA
+    int a, b;
+    mortar_ab(typ, pos, a, b);
+    const int oinv = mvirt[v - vbase].w;
+    // transpose of the pass along p: sT[j][m] = sum_i P^a[i][m] sB[j][i]
+    for (int t = tid; t < n2; t += kMortarThreads) {
+      const int j = t / n, m = t - j * n;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        real y;
+        if (typ & 1) {
+          y = real(0);
+#pragma unroll
+          for (int i = 0; i < n; ++i) y += mo.P[a][i * n + m] * sB[c * n2 + j * n + i];
+        } else {
+          y = sB[c * n2 + t];
+        }
+        sT[c * n2 + t] = y;
+      }
+    }
+    __syncthreads();
+    // transpose of the pass along q: y[be][m] = sum_j P^b[j][be] sT[j][m], at sub node (m, be)
+    for (int t = tid; t < n2; t += kMortarThreads) {
+      const int be = t / n, m = t - be * n;
+      const int spq = orient_pq(oinv, n - 1, m, be);
+      real y[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        if (typ & 2) {
+          y[c] = real(0);
+#pragma unroll
+          for (int j = 0; j < n; ++j) y[c] += mo.P[b][j * n + be] * sT[c * n2 + j * n + m];
+        } else {
+          y[c] = sT[c * n2 + t];
+        }
+      }
+      if constexpr (KIND == 1) {
+#pragma unroll
+        for (int c = 0; c < NV; ++c) Lv[((size_t)(S + v) * NV + c) * n2 + spq] = y[c];
+      } else {
+        const real* g = fgeo + ((size_t)v * 4) * n2 + spq;
+        const real sa = g[3 * n2];
+#pragma unroll
+        for (int c = 0; c < NV; ++c)
+          Lv[((size_t)(S + v) * NV + c) * n2 + spq] =
+              -sa * (g[0] * y[c * 3] + g[n2] * y[c * 3 + 1] + g[2 * n2] * y[c * 3 + 2]);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
 // launcher: forward recompute + reverse sweep
 // ---------------------------------------------------------------------------
 struct AdjScratch {
-  void *LF, *LWf, *LGf, *LWs, *muv;
+  void *LF, *LWf, *LGf, *LWs, *muv, *LQB;
 };
 
 inline AdjScratch adj_layout(const DevMesh& m, void* base, size_t rs) {
@@ -947,7 +1133,8 @@ inline AdjScratch adj_layout(const DevMesh& m, void* base, size_t rs) {
   a.LWf = p; p += sf5;
   a.LGf = p; p += sf15;
   a.LWs = p; p += sf5;
-  a.muv = p;
+  a.muv = p; p += (size_t)m.K * NV * m.n * m.n * m.n * rs;
+  a.LQB = p;  // [nBig][15][n^2]
   return a;
 }
 
@@ -960,34 +1147,47 @@ static cudaError_t launch_adj_vol(const DevMesh& m, const real* U, const real* l
   if (err != cudaSuccess) return err;
   k_adj_vol<real, n, BR2, SPLIT><<<grid, Cfg<n>::T, smem, st>>>(
       U, (const real*)m.Ja, (const real*)m.sJ, (const real*)m.Gvol, (const real*)m.fgeo, m.elemSide, lam,
-      (const real*)a.LGf, (real*)a.LWs, (real*)a.LWf, (real*)a.muv, m.K, m.S, ops, ph);
+      (const real*)a.LGf, (real*)a.LWs, (real*)a.LWf, (real*)a.muv, m.K, m.S, m.Sface, (real*)a.LQB, ops, ph);
   return cudaGetLastError();
 }
 
 template <typename real, int n>
 static cudaError_t rhs_adjoint_n(const DevMesh& m, const real* U, const real* lam, real* out, real scale,
-                                 int accumulate, const Ops<real>& ops, const Phys<real>& ph, void* scratch, double t,
-                                 cudaStream_t st) {
+                                 int accumulate, const Ops<real>& ops, const MortarOps<real>& mo, const Phys<real>& ph,
+                                 void* scratch, double t, cudaStream_t st) {
   using C = Cfg<n>;
   const int grid = (m.K + C::NE - 1) / C::NE;
   const int sgrid = (m.S * n * n + 127) / 128;
+  const int fgrid = (m.Sface * n * n + 127) / 128;
   AdjScratch a = adj_layout(m, scratch, sizeof(real));
+  const int4* mv = (const int4*)m.mvirt;
   cudaError_t err;
-  // forward recompute of face states, face gradients and volume gradients
+  // forward recompute of face states, face gradients and volume gradients (and,
+  // on mortar meshes, the virtual sides' interpolated states and gradients and QB)
   if ((err = prolong_n<real, n>(m, U, ops, ph, st)) != cudaSuccess) return err;
   if ((err = launch_bc<real>(m, t, ph, st)) != cudaSuccess) return err;
+  if ((err = launch_mortar_state<real>(m, mo, ph, st)) != cudaSuccess) return err;
   if (m.br2) {
     if ((err = lift_vol_n<real, n, 0, false, 0, true>(m, U, ops, ph, 1, st)) != cudaSuccess) return err;
   } else {
     if ((err = lift_vol_n<real, n, 0>(m, U, ops, ph, 1, st)) != cudaSuccess) return err;
   }
+  if ((err = launch_mortar_grad<real>(m, mo, ph, st)) != cudaSuccess) return err;
   k_adj_lamface<real, n><<<grid, C::T, 0, st>>>(lam, (const real*)m.sJ, m.elemSide, (real*)a.LF, m.K, m.S, ops);
+  if (m.nBig > 0)  // the big element's flux adjoint to slot 1 of its virtual sides
+    k_adj_mortar_project<real, n, 1><<<m.nBig, kMortarThreads, 0, st>>>((const real*)a.LF, (real*)a.LF, nullptr,
+                                                                       m.mbig, mv, m.S, m.Sface, m.vbase, mo);
   if (ph.riemann == 0 || ph.riemann == 2)
-    k_adj_face<real, n, false><<<sgrid, 128, 0, st>>>((const real*)m.Wf, (const real*)m.Gf, (const real*)m.fgeo,
-                                                      (const real*)a.LF, (real*)a.LWf, (real*)a.LGf, m.S, m.nBC, ph);
+    k_adj_face<real, n, false><<<fgrid, 128, 0, st>>>((const real*)m.Wf, (const real*)m.Gf, (const real*)m.fgeo,
+                                                      (const real*)a.LF, (real*)a.LWf, (real*)a.LGf, m.S, m.nBC,
+                                                      m.Sface, ph);
   else
-    k_adj_face<real, n, true><<<sgrid, 128, 0, st>>>((const real*)m.Wf, (const real*)m.Gf, (const real*)m.fgeo,
-                                                     (const real*)a.LF, (real*)a.LWf, (real*)a.LGf, m.S, m.nBC, ph);
+    k_adj_face<real, n, true><<<fgrid, 128, 0, st>>>((const real*)m.Wf, (const real*)m.Gf, (const real*)m.fgeo,
+                                                     (const real*)a.LF, (real*)a.LWf, (real*)a.LGf, m.S, m.nBC,
+                                                     m.Sface, ph);
+  if (m.nBig > 0)  // virtual sides' gradient adjoints (slot 1) to the big element's face gradient
+    k_adj_mortar_interp<real, n, 15, false><<<m.nBig, kMortarThreads, 0, st>>>((real*)a.LGf, m.mbig, mv, m.S,
+                                                                              m.Sface, m.vbase, mo);
   if (m.br2) {
     if ((err = launch_adj_vol<real, n, true, 0>(m, U, lam, a, ops, ph, grid, st)) != cudaSuccess) return err;
   } else if (m.split == 1) {
@@ -997,8 +1197,15 @@ static cudaError_t rhs_adjoint_n(const DevMesh& m, const real* U, const real* la
   } else {
     if ((err = launch_adj_vol<real, n, false, 0>(m, U, lam, a, ops, ph, grid, st)) != cudaSuccess) return err;
   }
+  if (m.nBig > 0)  // adjoint of QB to U* of the virtual sides (slot 1 of LWs)
+    k_adj_mortar_project<real, n, 0><<<m.nBig, kMortarThreads, 0, st>>>((const real*)a.LQB, (real*)a.LWs,
+                                                                       (const real*)m.fgeo, m.mbig, mv, m.S,
+                                                                       m.Sface, m.vbase, mo);
   k_adj_side<real, n><<<sgrid, 128, 0, st>>>((const real*)m.Wf, (const real*)a.LWs, (const real*)m.fgeo, m.bcKind,
-                                             (real*)a.LWf, m.S, m.nBC, ph);
+                                             (real*)a.LWf, m.S, m.nBC, m.Sface, ph);
+  if (m.nBig > 0)  // interpolated states' adjoints (slot 1, conservative) to the big element's face state
+    k_adj_mortar_interp<real, n, NV, true><<<m.nBig, kMortarThreads, 0, st>>>((real*)a.LWf, m.mbig, mv, m.S,
+                                                                             m.Sface, m.vbase, mo);
   k_adj_gather<real, n><<<grid, C::T, 0, st>>>((const real*)a.LWf, m.elemSide, (const real*)a.muv, out, scale,
                                                accumulate, m.K, m.S, ops);
   return cudaGetLastError();
@@ -1006,8 +1213,9 @@ static cudaError_t rhs_adjoint_n(const DevMesh& m, const real* U, const real* la
 
 template <typename real>
 cudaError_t launch_rhs_adjoint(const DevMesh& m, const real* U, const real* lam, real* out, real scale, int accumulate,
-                               const Ops<real>& ops, const Phys<real>& ph, void* scratch, double t, cudaStream_t st) {
-  FLEXI_DISPATCH_N(m.n, return rhs_adjoint_n<real, NN>(m, U, lam, out, scale, accumulate, ops, ph, scratch, t, st));
+                               const Ops<real>& ops, const MortarOps<real>& mo, const Phys<real>& ph, void* scratch,
+                               double t, cudaStream_t st) {
+  FLEXI_DISPATCH_N(m.n, return rhs_adjoint_n<real, NN>(m, U, lam, out, scale, accumulate, ops, mo, ph, scratch, t, st));
   return cudaSuccess;
 }
 

@@ -91,8 +91,8 @@ cudaError_t launch_surf(const DevMesh& m, int mode, real* U, real* dU, real* Ut,
 // launch_lift_vol with store_grad = 1); mode 1 accumulates out += scale * result
 template <typename real>
 cudaError_t launch_rhs_adjoint(const DevMesh& m, const real* U, const real* lam, real* out, real scale,
-                               int accumulate, const Ops<real>& ops, const Phys<real>& ph, void* scratch,
-                               double t, cudaStream_t st);
+                               int accumulate, const Ops<real>& ops, const MortarOps<real>& mo,
+                               const Phys<real>& ph, void* scratch, double t, cudaStream_t st);
 size_t adjoint_scratch_bytes(const DevMesh& m, size_t real_size);
 template <typename real>
 cudaError_t launch_axpby(real* y, const real* x, real a, real b, size_t count, cudaStream_t st);

@@ -165,9 +165,59 @@ def test_mortar_errors():
 
         Solver(SolverConfig(N=2), mesh.coords, mesh.conn, device=DEV)
     assert ei.value.code == F.FLEXI_EMESH
-    s = _solver(dict(N=2, riemann=0, adjoint=True), mesh)
+    s = _solver(dict(N=2, riemann=0, adjoint=True, lifting=1), mesh)  # BR2 adjoint: not on mortar meshes
     U = torch.tensor(wl.freestream(mesh.node_coords(2, 0)), device=DEV)
     with pytest.raises(F.FlexiError) as ei:
         F.flexi_rhs_adjoint(s.ctx, U, torch.ones_like(U), torch.empty_like(U), 0.0, torch.cuda.current_stream())
     s.close()
     assert ei.value.code == F.FLEXI_EUNSUPPORTED
+
+
+ADJ_CASES = [
+    ("t1_lg_N3_roesmooth", dict(refine=(1, 2, 1), ny=1, nz=2, reorient_seed=1), dict(N=3, riemann=2, mu=1 / 400.0)),
+    ("t3_lgl_N4_hllc", dict(refine=(1, 2, 2), ny=1, nz=1, reorient_seed=5),
+     dict(N=4, node_type=1, riemann=1, mu=1 / 400.0)),
+    ("t2_curved_lg_N2_rusanov", dict(refine=(1, 1, 2), ny=2, nz=1, reorient_seed=2, mapping="sine", Ngeo=2),
+     dict(N=2, Ngeo=2, riemann=3, mu=1 / 400.0)),
+    ("t3_split_lgl_N3", dict(refine=(2, 2, 2), ny=1, nz=1, reorient_seed=8),
+     dict(N=3, node_type=1, riemann=1, split_form=1, mu=1 / 400.0)),
+    ("t2_dirichlet_mms_N3", dict(refine=(1, 1, 2), ny=1, nz=2, reorient_seed=9, periodic=(False, True, True),
+                                 mapping="sine", Ngeo=3),
+     dict(N=3, Ngeo=3, riemann=2, bc_exact=2, source=True, mu=1 / 400.0)),
+]
+
+
+@pytest.mark.parametrize("name,mk,sk", ADJ_CASES, ids=[c[0] for c in ADJ_CASES])
+def test_mortar_rhs_adjoint_vs_oracle(name, mk, sk):
+    """Discrete adjoint on mortar meshes: the transposed interpolation of the big
+    side's state and gradients and the transposed projections of its lifting and
+    numerical fluxes, against the oracle's reverse-mode derivative."""
+    mesh = wl.mortar_box_mesh(**mk)
+    s = _solver(dict(sk, adjoint=True), mesh)
+    dg = _oracle(sk, mesh)
+    U0 = _state(mesh, sk["N"], sk.get("node_type", 0), "manufactured" if sk.get("source") else "perturbed")
+    lam = np.random.default_rng(6).normal(size=U0.shape)
+    out = s.rhs_adjoint(torch.tensor(U0, device=DEV), torch.tensor(lam, device=DEV), 0.1)
+    ref = dg.rhs_vjp(torch.tensor(U0), 0.1, torch.tensor(lam))
+    s.close()
+    d = (out.cpu() - ref).transpose(0, 1).reshape(5, -1).norm(dim=1)
+    r = ref.transpose(0, 1).reshape(5, -1).norm(dim=1)
+    assert float((d / r).max()) < 1e-10, (d / r).tolist()
+
+
+@pytest.mark.parametrize("ci", [0, 2])
+def test_mortar_adjoint_dot_product(ci):
+    """Central-difference dot-product test on a mortar mesh (no oracle)."""
+    name, mk, sk = ADJ_CASES[ci]
+    mesh = wl.mortar_box_mesh(**mk)
+    s = _solver(dict(sk, adjoint=True), mesh)
+    U0 = torch.tensor(_state(mesh, sk["N"], sk.get("node_type", 0)), device=DEV)
+    g = torch.Generator(device="cpu").manual_seed(8)
+    v = torch.randn(U0.shape, generator=g, dtype=torch.float64).to(DEV)
+    lam = torch.randn(U0.shape, generator=g, dtype=torch.float64).to(DEV)
+    eps = 1e-6
+    Jv = (s.rhs(U0 + eps * v, 0.1) - s.rhs(U0 - eps * v, 0.1)) / (2 * eps)
+    a = float((lam * Jv).sum())
+    b = float((s.rhs_adjoint(U0, lam, 0.1) * v).sum())
+    s.close()
+    assert abs(a - b) < 1e-6 * abs(b), (a, b)
