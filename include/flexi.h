@@ -141,7 +141,7 @@ flexi_status flexi_mesh_init(flexi_ctx **out, const flexi_params *p, int K, cons
  * to the small sides (I^L, I^U), the numerical and BR1 lifting fluxes are
  * computed there and L2-projected back (P^L, P^U).  Returns FLEXI_EMESH for
  * inconsistent mortar rows; otherwise as flexi_mesh_init.  The discrete adjoint
- * covers mortar meshes with BR1 lifting (BR2 there: FLEXI_EUNSUPPORTED). */
+ * covers mortar meshes. */
 #define FLEXI_CONN_MORTAR (-1073741824)
 flexi_status flexi_mesh_init_mortar(flexi_ctx **out, const flexi_params *p, int K, const double *coords,
                                     const int32_t *conn, int M, const int32_t *mortars, void *stream);
@@ -185,8 +185,8 @@ flexi_status flexi_rk_step_stages(flexi_ctx *ctx, void *U, void *dU, double t, d
  * standard or the split-form volume integral; every numerical flux (the Roe fluxes by a
  * hand-written reverse, HLLC, Rusanov and EC in forward mode); periodic meshes
  * and meshes with boundaries of every kind (the outer state's dependence on the
- * inner one is transposed; a source term does not depend on U); mortar meshes
- * with BR1 (FLEXI_EUNSUPPORTED otherwise). */
+ * inner one is transposed; a source term does not depend on U) and mortar
+ * meshes (FLEXI_EUNSUPPORTED for the tensor-core precisions). */
 flexi_status flexi_adjoint_step(flexi_ctx *ctx, const void *U_stages, void *lamU, void *lam_dU, double t,
                                 double dt, void *stream);
 

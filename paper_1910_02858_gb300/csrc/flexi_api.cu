@@ -771,8 +771,10 @@ flexi_status flexi_rk_step_stages(flexi_ctx* c, void* U, void* dU, double t, dou
                  : do_rk_step<float>(c, (float*)U, (float*)dU, t, dt, (float*)U_stages, st);
 }
 
+// every form, flux, lifting, boundary kind and mortar mesh; the FP64 and FP32
+// forms (the tensor-core sweeps have no reverse)
 static bool adjoint_supported(const flexi_ctx* c) {
-  return c->p.adjoint && (c->nMortar == 0 || c->p.lifting == FLEXI_LIFTING_BR1);
+  return c->p.adjoint != 0 && (c->p.precision == FLEXI_FP64 || c->p.precision == FLEXI_FP32);
 }
 
 flexi_status flexi_adjoint_step(flexi_ctx* c, const void* U_stages, void* lamU, void* lam_dU, double t, double dt,

@@ -480,8 +480,18 @@ __global__ void __launch_bounds__(128) k_adj_face(const real* __restrict__ Wf, c
                                                   int nFace, Phys<real> ph) {
   constexpr int n2 = n * n;
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= nFace * n2) return;  // sides 0 .. nFace-1 carry a numerical flux (not the big sides of mortars)
+  if (idx >= S * n2) return;
   const int side = idx / n2, pq = idx - side * n2;
+  if (side >= nFace) {  // big side of a mortar (no numerical flux of its own): start its adjoints at zero
+#pragma unroll
+    for (int slot = 0; slot < 2; ++slot) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) LWf[((size_t)(slot * S + side) * NV + v) * n2 + pq] = real(0);
+#pragma unroll
+      for (int c = 0; c < 15; ++c) LGf[((size_t)(slot * S + side) * 15 + c) * n2 + pq] = real(0);
+    }
+    return;
+  }
   const bool bnd = side < nBC;  // boundary side: no slave element, outer gradient = inner gradient
   real WL[NV], WR[NV], GL[15], GR[15], nv[3], lf[NV];
   const real sa = fgeo[((size_t)side * 4 + 3) * n2 + pq];
@@ -750,6 +760,7 @@ __global__ void __launch_bounds__(Cfg<n>::T) k_adj_vol(
         for (int a = 0; a < n; ++a) kap += lw[a] * lv[a] * sSJ[el2 * n3 + vol_index(l, a, p, q, n)];
         const real ek = ph.eta_br2 * kap;
         real* own = LWf + ((size_t)(es_slave(es) * S + side) * NV) * n2 + mpq;
+        const bool big = side >= bigBase;  // big side of a mortar: the jump's U* n s_hat is QB
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
           real acc = real(0);
@@ -760,9 +771,10 @@ __global__ void __launch_bounds__(Cfg<n>::T) k_adj_vol(
 #pragma unroll
             for (int a = 0; a < n; ++a) lJ -= lv[a] * b[c * n3 + vol_index(l, a, p, q, n)];
             acc += nd[d] * lJ;
+            if (big) LQB[((size_t)(side - bigBase) * 15 + v * 3 + d) * n2 + mpq] = lJ;  // -> QB
           }
-          sBr[((el2 * 6 + s) * NV + v) * n2 + pq] = acc;  // -> U* (both sides' mean)
-          own[v * n2] -= acc;                             // -> the element's own face state
+          sBr[((el2 * 6 + s) * NV + v) * n2 + pq] = big ? real(0) : acc;  // -> U* (both sides' mean)
+          own[v * n2] -= acc;  // -> the element's own face state
         }
       }
     }
@@ -822,7 +834,7 @@ __global__ void __launch_bounds__(Cfg<n>::T) k_adj_vol(
             real sdv = real(0);
 #pragma unroll
             for (int a = 0; a < n; ++a) sdv += lv[a] * b[(d * NV + v) * n3 + vol_index(l, a, p, q, n)];
-            lq[(v * 3 + d) * n2] = sdv;
+            lq[(v * 3 + d) * n2] = BR2 ? lq[(v * 3 + d) * n2] + sdv : sdv;  // BR2: the jump's part first
           }
       }
     }
@@ -848,10 +860,19 @@ __global__ void __launch_bounds__(128) k_adj_side(const real* __restrict__ Wf, c
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= S * n2) return;
   const int side = idx / n2, pq = idx - side * n2;
-  if (side >= bigBase) {  // big side of a mortar: its state reaches the flux only through the
-#pragma unroll            // interpolation, whose transpose k_adj_mortar_interp adds afterwards
+  if (side >= bigBase) {  // big side of a mortar: its state reaches the fluxes through the
+    // interpolation (transposed by k_adj_mortar_interp afterwards) and, with BR2, the
+    // big element's own jumps (slot 0 of LWf, from k_adj_vol)
+    real W[NV], lW[NV], lU[NV] = {0, 0, 0, 0, 0};
+#pragma unroll
     for (int v = 0; v < NV; ++v) {
-      LWf[((size_t)side * NV + v) * n2 + pq] = real(0);
+      W[v] = Wf[((size_t)side * NV + v) * n2 + pq];
+      lW[v] = LWf[((size_t)side * NV + v) * n2 + pq];
+    }
+    prim_vjp(W, lW, ph, lU);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      LWf[((size_t)side * NV + v) * n2 + pq] = lU[v];
       LWf[((size_t)(S + side) * NV + v) * n2 + pq] = real(0);
     }
     return;
@@ -1158,7 +1179,6 @@ static cudaError_t rhs_adjoint_n(const DevMesh& m, const real* U, const real* la
   using C = Cfg<n>;
   const int grid = (m.K + C::NE - 1) / C::NE;
   const int sgrid = (m.S * n * n + 127) / 128;
-  const int fgrid = (m.Sface * n * n + 127) / 128;
   AdjScratch a = adj_layout(m, scratch, sizeof(real));
   const int4* mv = (const int4*)m.mvirt;
   cudaError_t err;
@@ -1178,11 +1198,11 @@ static cudaError_t rhs_adjoint_n(const DevMesh& m, const real* U, const real* la
     k_adj_mortar_project<real, n, 1><<<m.nBig, kMortarThreads, 0, st>>>((const real*)a.LF, (real*)a.LF, nullptr,
                                                                        m.mbig, mv, m.S, m.Sface, m.vbase, mo);
   if (ph.riemann == 0 || ph.riemann == 2)
-    k_adj_face<real, n, false><<<fgrid, 128, 0, st>>>((const real*)m.Wf, (const real*)m.Gf, (const real*)m.fgeo,
+    k_adj_face<real, n, false><<<sgrid, 128, 0, st>>>((const real*)m.Wf, (const real*)m.Gf, (const real*)m.fgeo,
                                                       (const real*)a.LF, (real*)a.LWf, (real*)a.LGf, m.S, m.nBC,
                                                       m.Sface, ph);
   else
-    k_adj_face<real, n, true><<<fgrid, 128, 0, st>>>((const real*)m.Wf, (const real*)m.Gf, (const real*)m.fgeo,
+    k_adj_face<real, n, true><<<sgrid, 128, 0, st>>>((const real*)m.Wf, (const real*)m.Gf, (const real*)m.fgeo,
                                                      (const real*)a.LF, (real*)a.LWf, (real*)a.LGf, m.S, m.nBC,
                                                      m.Sface, ph);
   if (m.nBig > 0)  // virtual sides' gradient adjoints (slot 1) to the big element's face gradient

@@ -26,7 +26,8 @@ def _oracle(sk, mesh):
     r = {0: ROE, 1: HLLC, 2: ROE, 3: RUSANOV}[sk.get("riemann", 0)]
     return DGSEM(Params(N=sk["N"], node_type=sk.get("node_type", 0), riemann=r, smooth_roe=sk.get("riemann", 0) == 2,
                         mu=sk.get("mu", 1 / 1600.0), bc_exact=sk.get("bc_exact", 0), source=sk.get("source", False),
-                        split="pirozzoli" if sk.get("split_form", 0) == 1 else ""),
+                        split="pirozzoli" if sk.get("split_form", 0) == 1 else "",
+                        lifting="br2" if sk.get("lifting", 0) == 1 else "br1", eta_br2=sk.get("eta_br2", 2.0)),
                  mesh.coords, mesh.conn, mesh.mortars)
 
 
@@ -165,8 +166,8 @@ def test_mortar_errors():
 
         Solver(SolverConfig(N=2), mesh.coords, mesh.conn, device=DEV)
     assert ei.value.code == F.FLEXI_EMESH
-    s = _solver(dict(N=2, riemann=0, adjoint=True, lifting=1), mesh)  # BR2 adjoint: not on mortar meshes
-    U = torch.tensor(wl.freestream(mesh.node_coords(2, 0)), device=DEV)
+    s = _solver(dict(N=2, riemann=0, adjoint=True, precision=2), mesh)  # no reverse of the tensor-core sweeps
+    U = torch.tensor(wl.freestream(mesh.node_coords(2, 0)), device=DEV, dtype=torch.float32)
     with pytest.raises(F.FlexiError) as ei:
         F.flexi_rhs_adjoint(s.ctx, U, torch.ones_like(U), torch.empty_like(U), 0.0, torch.cuda.current_stream())
     s.close()
@@ -184,6 +185,10 @@ ADJ_CASES = [
     ("t2_dirichlet_mms_N3", dict(refine=(1, 1, 2), ny=1, nz=2, reorient_seed=9, periodic=(False, True, True),
                                  mapping="sine", Ngeo=3),
      dict(N=3, Ngeo=3, riemann=2, bc_exact=2, source=True, mu=1 / 400.0)),
+    ("t3_br2_lg_N3_hllc", dict(refine=(1, 2, 2), ny=1, nz=1, reorient_seed=3),
+     dict(N=3, riemann=1, lifting=1, eta_br2=2.0, mu=1 / 400.0)),
+    ("t1_br2_lgl_N4_eta5", dict(refine=(1, 2, 1), ny=1, nz=2, reorient_seed=6, mapping="sine", Ngeo=2),
+     dict(N=4, Ngeo=2, node_type=1, riemann=2, lifting=1, eta_br2=5.0, mu=1 / 400.0)),
 ]
 
 
