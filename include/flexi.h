@@ -29,6 +29,9 @@
  *    reported by the next flexi_reduce or flexi_query(FLEXI_Q_STATUS).
  *  - Errors are returned as flexi_status codes; nothing is thrown across the
  *    ABI and nothing exits the process.  flexi_strerror gives the text.
+ *  - A context belongs to the CUDA device that was current at flexi_mesh_init.
+ *    Every call that launches work or copies data returns FLEXI_EINVAL, before
+ *    touching the GPU, when another device is current in the calling thread.
  *  - No call allocates device buffers after flexi_mesh_init (flexi_rk_run_host
  *    stages through buffers allocated there); flexi_rk_run instantiates a CUDA
  *    graph, a driver resource, when it first replays a step.
@@ -217,8 +220,11 @@ flexi_status flexi_reduce(flexi_ctx *ctx, const void *U, const void *Ut, double 
  * static device memory instead of a context buffer, and calls no allocating
  * routine.  The paper has no counterpart of this call.
  *   - Limit: K <= FLEXI_NOALLOC_MAX_ELEMENTS elements; larger meshes return
- *     FLEXI_EINVAL.  The static array (about 4.5 MiB) is held by every GPU
- *     that loads the library until the process exits.
+ *     FLEXI_EINVAL.  One thread per node: n^3 <= 512 (N <= 7, the library's
+ *     limit), else FLEXI_EUNSUPPORTED.  The static array (about 4.5 MiB) is held
+ *     by every GPU that loads the library until the process exits.
+ *   - The static array used is the one of the current device, which must be
+ *     the context's (else FLEXI_EINVAL, before any launch).
  *   - The first call on a device looks up the array's device address (once per
  *     device); make that first call before any stream capture.
  *   - All calls share the array: calls whose work overlaps on the GPU (several

@@ -95,9 +95,17 @@ class MeshGeometry:
 
         X = interp(X0, xgeo, basis.x_np)
         self.x = X  # [K, 3, n, n, n] at the solution nodes
+        # The metric terms and J are invariant under a translation of the mapping
+        # (grad_xi of a constant vanishes, and curl_xi(c grad_xi x_m) = 0 because the
+        # tensor-product derivatives along different directions commute), so they
+        # are formed from each element's coordinates relative to its first geometry
+        # node: differentiating absolute coordinates that are large compared with
+        # the element's width would cancel digits in every sum.
+        X0r = X0 - X0[:, :, :1, :1, :1]
         D = basis.D
         # dx[e, c, l, k, j, i] = d x_c / d xi_l at the solution nodes
-        dx = torch.stack([apply_dir(D, X, l) for l in range(3)], dim=2)
+        Xr = interp(X0r, xgeo, basis.x_np)
+        dx = torch.stack([apply_dir(D, Xr, l) for l in range(3)], dim=2)
         Jm = dx.permute(0, 3, 4, 5, 1, 2)  # [K, k, j, i, c, l]
         self.J = torch.linalg.det(Jm)
         # curl form metrics, collocated on the degree-N Lobatto points (whose
@@ -105,7 +113,7 @@ class MeshGeometry:
         # face metrics), then interpolated (exactly, degree N) to the solution nodes
         xl, _ = lobatto_nodes(N)
         Dl = torch.tensor(diff_matrix(xl), dtype=DT)
-        XL = interp(X0, xgeo, xl)
+        XL = interp(X0r, xgeo, xl)
         dxl = torch.stack([apply_dir(Dl, XL, l) for l in range(3)], dim=2)
         JaL = torch.zeros(K, 3, 3, n, n, n, dtype=DT)
         for nn in range(3):

@@ -33,6 +33,7 @@ enum { KC_LIFTVOL = 0, KC_FACE = 1, KC_SURF = 2, KC_PROLONG = 3, KC_BC = 4, KC_A
 
 struct flexi_ctx {
   flexi_params p{};
+  int device = -1;  // the CUDA device current at flexi_mesh_init; every call must run with it current
   int K = 0, N = 0, n = 0, n2 = 0, n3 = 0, S = 0, nBC = 0;
   bool fp64 = true;
   size_t rs = 8;
@@ -76,6 +77,12 @@ struct flexi_ctx {
 namespace {
 
 flexi_status cuda_status(cudaError_t e) { return e == cudaSuccess ? FLEXI_OK : FLEXI_ECUDA; }
+
+// the calling thread's current device is the one the context's buffers live on
+bool on_ctx_device(const flexi_ctx* c) {
+  int d = -1;
+  return cudaGetDevice(&d) == cudaSuccess && d == c->device;
+}
 
 #define CK(expr)                                   \
   do {                                             \
@@ -275,6 +282,7 @@ void fill_mortar_ops(MortarOps<real>& o, const std::vector<double>& x, const std
 
 flexi_status mesh_init_impl(flexi_ctx* c, const flexi_params* p, int K, const double* coords, const int32_t* conn,
                             int M, const int32_t* mortars, cudaStream_t st) {
+  if (cudaGetDevice(&c->device) != cudaSuccess) return FLEXI_ECUDA;
   c->p = *p;
   c->K = K;
   c->N = p->N;
@@ -440,10 +448,11 @@ flexi_status mesh_init_impl(flexi_ctx* c, const flexi_params* p, int K, const do
   };
   auto free_tmp = [&]() { for (void* q : tmp) cudaFree(q); tmp.clear(); };
   struct Guard { decltype(free_tmp)& f; ~Guard() { f(); } } guard{free_tmp};
-  double *X0, *A1, *A2, *XL, *dXL[3], *v, *dA, *dB, *JaL, *X, *dX[3], *dMat, *wdev;
+  double *X0, *X0r, *A1, *A2, *XL, *dXL[3], *v, *dA, *dB, *JaL, *X, *Xr, *dX[3], *dMat, *wdev;
   int* sideM;
 #define TA(ptr, cnt) if ((s = talloc(&(ptr), (cnt))) != FLEXI_OK) return s
   TA(X0, (size_t)K * 3 * ng3);
+  TA(X0r, (size_t)K * 3 * ng3);
   TA(A1, (size_t)K * 9 * n3);
   TA(A2, (size_t)K * 9 * n3);
   TA(XL, (size_t)K * 3 * n3);
@@ -453,6 +462,7 @@ flexi_status mesh_init_impl(flexi_ctx* c, const flexi_params* p, int K, const do
   TA(dB, (size_t)K * n3);
   TA(JaL, (size_t)K * 9 * n3);
   TA(X, (size_t)K * 3 * n3);
+  TA(Xr, (size_t)K * 3 * n3);
   for (int l = 0; l < 3; ++l) TA(dX[l], (size_t)K * 3 * n3);
   TA(dMat, 6 * 64 + 16);
   TA(wdev, 16);
@@ -462,13 +472,22 @@ flexi_status mesh_init_impl(flexi_ctx* c, const flexi_params* p, int K, const do
     tmp.push_back(q);
     sideM = (int*)q;
   }
-  // coordinates: [K][kg][jg][ig][3] -> [K][3][kg][jg][ig]
+  // coordinates: [K][kg][jg][ig][3] -> [K][3][kg][jg][ig], absolute (X0: node positions
+  // for boundary states and source terms) and relative to the element's first geometry
+  // node (X0r: metric terms and J, which do not change under a translation of the
+  // mapping; differentiating absolute coordinates that are large compared with the
+  // element's width would cancel digits in every sum)
   {
-    std::vector<double> h((size_t)K * 3 * ng3);
+    std::vector<double> h((size_t)K * 3 * ng3), hr((size_t)K * 3 * ng3);
     for (int e = 0; e < K; ++e)
       for (int node = 0; node < ng3; ++node)
-        for (int d = 0; d < 3; ++d) h[((size_t)e * 3 + d) * ng3 + node] = coords[((size_t)e * ng3 + node) * 3 + d];
+        for (int d = 0; d < 3; ++d) {
+          const double x = coords[((size_t)e * ng3 + node) * 3 + d];
+          h[((size_t)e * 3 + d) * ng3 + node] = x;
+          hr[((size_t)e * 3 + d) * ng3 + node] = x - coords[(size_t)e * ng3 * 3 + d];
+        }
     CK(cudaMemcpyAsync(X0, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(X0r, hr.data(), hr.size() * sizeof(double), cudaMemcpyHostToDevice, st));
     CK(cudaStreamSynchronize(st));
   }
   // operator matrices on the device: Vg2l, Dl, Vl2s, Vg2s, Ds (each <= 64 entries)
@@ -499,7 +518,7 @@ flexi_status mesh_init_impl(flexi_ctx* c, const flexi_params* p, int K, const do
   };
   // curl-form metrics on the degree-N Lobatto points (face metrics of the two
   // elements of a side then agree), interpolated to the solution nodes
-  CK(interp3(X0, XL, dVg2l, 3 * K, ng));
+  CK(interp3(X0r, XL, dVg2l, 3 * K, ng));
   for (int l = 0; l < 3; ++l) CK(geom_apply1d(XL, dXL[l], dDl, 3 * K, n, n, n, l, n, st));
   CK(geom_metric_products(XL, dXL, v, K, n3, st));
   const size_t blk = (size_t)K * n3;
@@ -513,7 +532,8 @@ flexi_status mesh_init_impl(flexi_ctx* c, const flexi_params* p, int K, const do
   CK(interp3(JaL, c->Ja64, dVl2s, 9 * K, n));
   // coordinates and Jacobian at the solution nodes
   CK(interp3(X0, X, dVg2s, 3 * K, ng));
-  for (int l = 0; l < 3; ++l) CK(geom_apply1d(X, dX[l], dDs, 3 * K, n, n, n, l, n, st));
+  CK(interp3(X0r, Xr, dVg2s, 3 * K, ng));
+  for (int l = 0; l < 3; ++l) CK(geom_apply1d(Xr, dX[l], dDs, 3 * K, n, n, n, l, n, st));
   CK(geom_jacobian(dX, c->sJ64, c->wJ, wdev, K, n, c->status, st));
   CK(geom_faces(c->Ja64, X, sideM, dlm, dlp, c->fgeo64, c->xbc, S, c->nBC, n, st));
   if (p->source) CK(cudaMemcpyAsync(c->xsol, X, (size_t)K * 3 * n3 * 8, cudaMemcpyDeviceToDevice, st));
@@ -647,6 +667,7 @@ bool ctx_reduce_inputs(const flexi_ctx* c, ReduceInputs* r) {
   if (c == nullptr || r == nullptr) return false;
   r->K = c->K;
   r->N = c->N;
+  r->device = c->device;
   r->n3 = c->n3;
   r->fp64 = c->fp64 ? 1 : 0;
   r->wJ = c->wJ;
@@ -738,6 +759,7 @@ flexi_status flexi_mesh_init_mortar(flexi_ctx** out, const flexi_params* p, int 
 
 flexi_status flexi_set_bc(flexi_ctx* c, int bc_id, int kind) {
   if (c == nullptr || kind < FLEXI_BC_EXACT || kind > FLEXI_BC_SLIP_WALL) return FLEXI_EINVAL;
+  if (!on_ctx_device(c)) return FLEXI_EINVAL;
   bool found = false;
   for (int b = 0; b < c->nBC; ++b)
     if (c->bcId[b] == bc_id) {
@@ -751,6 +773,7 @@ flexi_status flexi_set_bc(flexi_ctx* c, int bc_id, int kind) {
 
 flexi_status flexi_rhs(flexi_ctx* c, const void* U, void* Ut, double t, void* stream) {
   if (c == nullptr || U == nullptr || Ut == nullptr) return FLEXI_EINVAL;
+  if (!on_ctx_device(c)) return FLEXI_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   return c->fp64 ? do_rhs<double>(c, (const double*)U, (double*)Ut, t, st)
                  : do_rhs<float>(c, (const float*)U, (float*)Ut, t, st);
@@ -758,6 +781,7 @@ flexi_status flexi_rhs(flexi_ctx* c, const void* U, void* Ut, double t, void* st
 
 flexi_status flexi_rk_step(flexi_ctx* c, void* U, void* dU, double t, double dt, void* stream) {
   if (c == nullptr || U == nullptr || dU == nullptr) return FLEXI_EINVAL;
+  if (!on_ctx_device(c)) return FLEXI_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   return c->fp64 ? do_rk_step<double>(c, (double*)U, (double*)dU, t, dt, nullptr, st)
                  : do_rk_step<float>(c, (float*)U, (float*)dU, t, dt, nullptr, st);
@@ -766,6 +790,7 @@ flexi_status flexi_rk_step(flexi_ctx* c, void* U, void* dU, double t, double dt,
 flexi_status flexi_rk_step_stages(flexi_ctx* c, void* U, void* dU, double t, double dt, void* U_stages,
                                   void* stream) {
   if (c == nullptr || U == nullptr || dU == nullptr || U_stages == nullptr) return FLEXI_EINVAL;
+  if (!on_ctx_device(c)) return FLEXI_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   return c->fp64 ? do_rk_step<double>(c, (double*)U, (double*)dU, t, dt, (double*)U_stages, st)
                  : do_rk_step<float>(c, (float*)U, (float*)dU, t, dt, (float*)U_stages, st);
@@ -780,6 +805,7 @@ static bool adjoint_supported(const flexi_ctx* c) {
 flexi_status flexi_adjoint_step(flexi_ctx* c, const void* U_stages, void* lamU, void* lam_dU, double t, double dt,
                                 void* stream) {
   if (c == nullptr || U_stages == nullptr || lamU == nullptr || lam_dU == nullptr) return FLEXI_EINVAL;
+  if (!on_ctx_device(c)) return FLEXI_EINVAL;
   if (!adjoint_supported(c)) return FLEXI_EUNSUPPORTED;
   cudaStream_t st = (cudaStream_t)stream;
   return c->fp64 ? do_adjoint_step<double>(c, (const double*)U_stages, (double*)lamU, (double*)lam_dU, t, dt, st)
@@ -788,6 +814,7 @@ flexi_status flexi_adjoint_step(flexi_ctx* c, const void* U_stages, void* lamU, 
 
 flexi_status flexi_rhs_adjoint(flexi_ctx* c, const void* U, const void* lam, void* out, double t, void* stream) {
   if (c == nullptr || U == nullptr || lam == nullptr || out == nullptr) return FLEXI_EINVAL;
+  if (!on_ctx_device(c)) return FLEXI_EINVAL;
   if (!adjoint_supported(c)) return FLEXI_EUNSUPPORTED;
   cudaStream_t st = (cudaStream_t)stream;
   return c->fp64 ? do_rhs_adjoint<double>(c, (const double*)U, (const double*)lam, (double*)out, 1.0, 0, t, st)
@@ -806,6 +833,7 @@ static bool autonomous(const flexi_ctx* c) {
 
 flexi_status flexi_rk_run(flexi_ctx* c, void* U, void* dU, int nsteps, double t0, double dt, void* stream) {
   if (c == nullptr || U == nullptr || dU == nullptr || nsteps < 0) return FLEXI_EINVAL;
+  if (!on_ctx_device(c)) return FLEXI_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   const bool use_graph = st != nullptr && !c->prof && autonomous(c) && nsteps > 1;
   int s = 0;
@@ -853,6 +881,7 @@ flexi_status flexi_rk_run(flexi_ctx* c, void* U, void* dU, int nsteps, double t0
 
 flexi_status flexi_rk_run_host(flexi_ctx* c, void* U_host, int nsteps, double t0, double dt, void* stream) {
   if (c == nullptr || U_host == nullptr || nsteps < 0) return FLEXI_EINVAL;
+  if (!on_ctx_device(c)) return FLEXI_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   const size_t bytes = (size_t)c->K * NV * c->n3 * c->rs;
   CK(cudaMemcpyAsync(c->Ustate, U_host, bytes, cudaMemcpyHostToDevice, st));
@@ -868,6 +897,7 @@ flexi_status flexi_rk_run_host(flexi_ctx* c, void* U_host, int nsteps, double t0
 
 flexi_status flexi_reduce(flexi_ctx* c, const void* U, const void* Ut, double cfl, double* out, void* stream) {
   if (c == nullptr || U == nullptr || out == nullptr) return FLEXI_EINVAL;
+  if (!on_ctx_device(c)) return FLEXI_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   const flexi_status s = c->fp64 ? do_reduce<double>(c, U, Ut, cfl, out, st) : do_reduce<float>(c, U, Ut, cfl, out, st);
   if (s != FLEXI_OK) return s;
@@ -908,6 +938,7 @@ flexi_status flexi_query(flexi_ctx* c, int what, int64_t* val) {
       return FLEXI_OK;
     }
     case FLEXI_Q_STATUS: {
+      if (!on_ctx_device(c)) return FLEXI_EINVAL;
       unsigned flag = 0;
       CK(cudaMemcpy(&flag, c->status, sizeof(unsigned), cudaMemcpyDeviceToHost));
       CK(cudaMemset(c->status, 0, sizeof(unsigned)));

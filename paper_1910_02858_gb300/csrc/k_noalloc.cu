@@ -31,12 +31,15 @@ constexpr int kQ = 9;  // 5 totals, kinetic energy, dKE/dt, max convective rate,
 
 static __device__ __align__(256) double g_noalloc_scratch[(kNoAllocMaxElements + 1) * kQ];
 
+constexpr int kElemThreads = 512;   // threads per element CTA: one per node, n^3 <= 512 (N <= 7)
+constexpr int kFinishThreads = 256;  // threads of the single CTA that sums the element partials
+
 // one CTA of 512 threads per element: FP64 sums over its n^3 <= 512 nodes -> partial[e][q]
 template <typename real>
 __global__ void k_reduce_elem(const real* __restrict__ U, const real* __restrict__ Ut, const double* __restrict__ wJ,
                               const double* __restrict__ Ja64, const double* __restrict__ sJ64,
                               double* __restrict__ partial, int n3, Phys<real> ph, double kv_coef) {
-  __shared__ double red[kQ][512];
+  __shared__ double red[kQ][kElemThreads];
   const long long e = blockIdx.x;
   const int node = threadIdx.x;
   double acc[kQ];
@@ -80,7 +83,7 @@ __global__ void k_reduce_elem(const real* __restrict__ U, const real* __restrict
 #pragma unroll
   for (int q = 0; q < kQ; ++q) red[q][threadIdx.x] = acc[q];
   __syncthreads();
-  for (int s = 256; s > 0; s >>= 1) {
+  for (int s = kElemThreads / 2; s > 0; s >>= 1) {
     if (threadIdx.x < s) {
 #pragma unroll
       for (int q = 0; q < 7; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + s];
@@ -94,11 +97,11 @@ __global__ void k_reduce_elem(const real* __restrict__ U, const real* __restrict
 
 // one CTA: sums the K element partials in a fixed order -> result[q]
 __global__ void k_reduce_finish(const double* __restrict__ partial, double* __restrict__ result, int K) {
-  __shared__ double red[kQ][1024];
+  __shared__ double red[kQ][kFinishThreads];
   double acc[kQ];
 #pragma unroll
   for (int q = 0; q < kQ; ++q) acc[q] = 0.0;
-  for (int e = threadIdx.x; e < K; e += 1024) {
+  for (int e = threadIdx.x; e < K; e += kFinishThreads) {
 #pragma unroll
     for (int q = 0; q < 7; ++q) acc[q] += partial[(long long)e * kQ + q];
     acc[7] = fmax(acc[7], partial[(long long)e * kQ + 7]);
@@ -107,7 +110,7 @@ __global__ void k_reduce_finish(const double* __restrict__ partial, double* __re
 #pragma unroll
   for (int q = 0; q < kQ; ++q) red[q][threadIdx.x] = acc[q];
   __syncthreads();
-  for (int s = 512; s > 0; s >>= 1) {
+  for (int s = kFinishThreads / 2; s > 0; s >>= 1) {
     if (threadIdx.x < s) {
 #pragma unroll
       for (int q = 0; q < 7; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + s];
@@ -146,10 +149,10 @@ static cudaError_t scratch_address(double** out) {
 template <typename real>
 static cudaError_t launch_noalloc(const ReduceInputs& in, const void* U, const void* Ut, const Phys<real>& ph,
                                   double* scratch, cudaStream_t st) {
-  // 512 threads (the tree below halves from 256): nodes beyond n^3 contribute zeros
-  k_reduce_elem<real><<<in.K, 512, 0, st>>>((const real*)U, (const real*)Ut, in.wJ, in.Ja64, in.sJ64, scratch,
+  // kElemThreads threads per element: nodes beyond n^3 contribute zeros
+  k_reduce_elem<real><<<in.K, kElemThreads, 0, st>>>((const real*)U, (const real*)Ut, in.wJ, in.Ja64, in.sJ64, scratch,
                                                 in.n3, ph, in.kv_coef);
-  k_reduce_finish<<<1, 1024, 0, st>>>(scratch, scratch + (size_t)kNoAllocMaxElements * kQ, in.K);
+  k_reduce_finish<<<1, kFinishThreads, 0, st>>>(scratch, scratch + (size_t)kNoAllocMaxElements * kQ, in.K);
   return cudaGetLastError();
 }
 
@@ -163,6 +166,9 @@ extern "C" flexi_status flexi_reduce_noalloc(flexi_ctx* ctx, const void* U, cons
   ReduceInputs in;
   if (!ctx_reduce_inputs(ctx, &in)) return FLEXI_EINVAL;
   if (in.K > kNoAllocMaxElements) return FLEXI_EINVAL;  // beyond the static array
+  if (in.n3 > kElemThreads) return FLEXI_EUNSUPPORTED;   // one thread per node in k_reduce_elem
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != in.device) return FLEXI_EINVAL;  // the context's device only
   double* scratch = nullptr;
   if (scratch_address(&scratch) != cudaSuccess) return FLEXI_ECUDA;
   cudaStream_t st = (cudaStream_t)stream;

@@ -110,6 +110,7 @@ namespace flexi {
 // read-only view of a context's inputs to the global reductions
 struct ReduceInputs {
   int K = 0, N = 0, n3 = 0, fp64 = 1;
+  int device = -1;  // the context's CUDA device
   const double *wJ = nullptr, *Ja64 = nullptr, *sJ64 = nullptr;
   const unsigned* status = nullptr;
   double kv_coef = 0;  // max(4/3, gamma/Pr) mu

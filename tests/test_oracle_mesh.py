@@ -79,3 +79,29 @@ def test_orientation_codes_all_used():
         for s in range(6):
             nb, ns, o = m.conn[e, s]
             assert tuple(m.conn[nb, ns, :2]) == (e, s)
+
+
+@pytest.mark.parametrize("node_type", [0, 1])
+def test_metrics_of_a_translated_mesh(node_type):
+    """The metric terms do not depend on where the mesh sits (Eq.
+    contravariantBasisVectorsCurl is invariant under translation) and keep their
+    closed-form values to round-off relative to the element's own size away from
+    the origin: a 2^3 Cartesian box of width pi (h/2 = pi/4) placed at x = 100 has
+    the same Ja and J as at the origin.  Differentiating the absolute coordinates
+    directly cancels digits of magnitude 100 into sums of magnitude h/2 (errors of
+    1e-12 in J and 3e-10 in Ja at N = 7); the bars below sit well above the
+    round-off of the coordinates themselves (ulp(100) / (h/2) = 2e-14)."""
+    N = 7
+    b = Basis(N, node_type)
+    h = math.pi / 2
+    far = wl.box_mesh((2, 2, 2), lo=(100.0,) * 3, hi=(100.0 + math.pi,) * 3, Ngeo=1, reorient_seed=4)
+    near = wl.box_mesh((2, 2, 2), lo=(0.0,) * 3, hi=(math.pi,) * 3, Ngeo=1, reorient_seed=4)
+    geo = MeshGeometry(b, far.coords, far.conn)
+    geo0 = MeshGeometry(b, near.coords, near.conn)
+    J = (h / 2) ** 3
+    assert (geo.J - J).abs().max() < 1e-13 * J
+    # rotated element frames permute and flip the rows Ja^i: Ja^T Ja = (h/2)^4 I at every node
+    G = torch.einsum("eadzyx,eafzyx->ezyxdf", geo.Ja, geo.Ja)
+    assert (G - torch.eye(3, dtype=G.dtype) * (h / 2) ** 4).abs().max() < 1e-12 * (h / 2) ** 4
+    assert (geo.Ja - geo0.Ja).abs().max() < 1e-12 * (h / 2) ** 2
+    assert (geo.x - geo0.x - 100.0).abs().max() < 1e-12
