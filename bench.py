@@ -94,7 +94,7 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -173,83 +173,128 @@ def algorithmic_per_dof(n: int, word: int):
     return bytes_stage, bytes_liftvol, flops_liftvol
 
 
-def run_cpu_baseline(budget_s: float = 20.0):
-    """The FP64 oracle as it stands, timed on the host cores on a bounded sample of
-    the same workload: repeated full right-hand sides of the 16^3, N=7 case."""
-    import torch
-
-    import workloads as wl
-    from oracle.dgsem import DGSEM, HLLC, Params
-
-    mesh = wl.box_mesh((16, 16, 16), Ngeo=1)
-    dg = DGSEM(Params(N=7, node_type=0, riemann=HLLC), mesh.coords, mesh.conn)
-    U = torch.tensor(wl.taylor_green(mesh.node_coords(7, 0)))
-    dof = dg.K * dg.n ** 3
-    dg.rhs(U)  # warm-up
-    t0 = time.perf_counter()
-    reps = 0
-    while True:
-        Ut = dg.rhs(U)
-        U2 = U + 1e-4 * Ut  # the stage update, so the sample is a full RK stage
-        reps += 1
-        if time.perf_counter() - t0 > budget_s / 2 or reps >= 10:
-            break
-    el = time.perf_counter() - t0
-    pid = el / (reps * dof) * 1e9
-    cores = torch.get_num_threads()
-    # the same oracle on one host thread, one stage
-    torch.set_num_threads(1)
+def host_cpu():
+    """Core count and CPU model of the host (the oracle runs on these cores)."""
+    model = None
     try:
-        t1 = time.perf_counter()
-        Ut = dg.rhs(U)
-        U2 = U + 1e-4 * Ut
-        pid1 = (time.perf_counter() - t1) / dof * 1e9
-    finally:
-        torch.set_num_threads(cores)
-    return {"value": pid, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{reps} RK stages (full RHS + update) of the 16^3 N=7 TGV workload, FP64 torch CPU",
-            "value_1_thread": pid1}
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().startswith("Model name:"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        import platform
+
+        model = platform.processor() or platform.machine()
+    return {"nproc": os.cpu_count(), "model": model}
 
 
-def reference_arm(args):
-    """--impl reference: the oracle timed as the reference arm on the host cores."""
-    world, rank, _ = dist_env()
-    if rank != 0:
-        return 0
+def time_oracle_stages(warmup: int, stages: int, threads=None):
+    """The FP64 oracle as it stands, on the host cores: full LSERK4(5) stages
+    (right-hand side + low-storage update) of the 16^3, N = 7 Taylor-Green
+    workload, after untimed warm-up stages.  Returns (PID, threads used, seconds)."""
     import torch
 
     import workloads as wl
-    from oracle.dgsem import DGSEM, HLLC, Params
+    from oracle.dgsem import DGSEM, HLLC, RK_A, RK_B, Params
 
+    if threads is not None:
+        torch.set_num_threads(threads)
     mesh = wl.box_mesh((16, 16, 16), Ngeo=1)
     dg = DGSEM(Params(N=7, node_type=0, riemann=HLLC), mesh.coords, mesh.conn)
     U = torch.tensor(wl.taylor_green(mesh.node_coords(7, 0)))
     dU = torch.zeros_like(U)
     dof = dg.K * dg.n ** 3
-    # one bench step of this arm = one RK stage (bounded sample of the workload)
-    from oracle.dgsem import RK_A, RK_B
 
     def stage(U, dU, k):
         Ut = dg.rhs(U)
         dU = RK_A[k % 5] * dU + 1e-4 * Ut
         return U + RK_B[k % 5] * dU, dU
 
-    for k in range(args.warmup):
+    for k in range(warmup):
         U, dU = stage(U, dU, k)
     t0 = time.perf_counter()
-    for k in range(args.steps):
+    for k in range(stages):
         U, dU = stage(U, dU, k)
     el = time.perf_counter() - t0
-    pid = el / (args.steps * dof) * 1e9
+    return el / (stages * dof) * 1e9, torch.get_num_threads(), el
+
+
+CPU_BASELINE_STAGES = (5, 20)  # warm-up and timed stages, all host cores
+CPU_BASELINE_STAGES_1T = (1, 3)  # the same on one host thread
+
+
+def run_cpu_baseline():
+    """CPU baseline of the native arm: the reference arm's own measurement (the
+    oracle on the host cores), run in fresh processes before any GPU work, so that
+    both arms time the same code in the same conditions; plus the one-thread figure."""
+    def arm(warmup, steps, threads=None):
+        cmd = [sys.executable, os.path.abspath(__file__), "--impl", "reference", "--steps", str(steps),
+               "--warmup", str(warmup)]
+        if threads is not None:
+            cmd += ["--threads", str(threads)]
+        env = {k: v for k, v in os.environ.items() if k not in ("RANK", "WORLD_SIZE", "LOCAL_RANK")}
+        out = subprocess.run(cmd, capture_output=True, text=True, timeout=900, env=env, cwd=ROOT)
+        for ln in out.stdout.splitlines()[::-1]:
+            if ln.startswith("{"):
+                return json.loads(ln)
+        raise RuntimeError(f"oracle timing failed: {out.stderr[-500:]}")
+
+    full = arm(*CPU_BASELINE_STAGES)
+    one = arm(*CPU_BASELINE_STAGES_1T, threads=1)
+    w, k = CPU_BASELINE_STAGES
+    return {"value": full["value"], "unit": UNIT, "cores": full["cpu_baseline"]["cores"], "kind": "oracle",
+            "sample": f"{k} RK stages (full RHS + low-storage update) of the 16^3 N=7 TGV workload after {w} "
+                      "warm-up stages, FP64 torch CPU, fresh process before any GPU work (the reference arm's code)",
+            "value_1_thread": one["value"],
+            "sample_1_thread": f"{CPU_BASELINE_STAGES_1T[1]} RK stages after {CPU_BASELINE_STAGES_1T[0]} warm-up, "
+                               "one host thread",
+            "host": host_cpu()}
+
+
+def reference_arm(args):
+    """--impl reference: the oracle timed as the reference arm on the host cores
+    (one bench step = one RK stage of the workload, a bounded sample of it)."""
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    pid, cores, el = time_oracle_stages(args.warmup, args.steps, args.threads)
     line = {"metric": METRIC, "value": pid, "unit": UNIT, "impl": "reference", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": dict(WORKLOAD, step="one RK stage (RHS + update) of the oracle"),
-            "cpu_baseline": {"value": pid, "unit": UNIT, "kind": "oracle", "cores": torch.get_num_threads(),
-                             "sample": f"{args.steps} RK stages of the 16^3 N=7 TGV workload"},
+            "cpu_baseline": {"value": pid, "unit": UNIT, "kind": "oracle", "cores": cores,
+                             "sample": f"{args.steps} RK stages of the 16^3 N=7 TGV workload after "
+                                       f"{args.warmup} warm-up stages", "host": host_cpu()},
             "e2e": {"value": pid, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def timed_steps(s, U, dU, dt, nsteps, F, torch, dev, t0=0.0):
+    """Event-timed LSERK4(5) steps on the library's stream with per-launch profiling
+    off (the product's launch stream), then the same number of steps again with the
+    library's per-launch events on, for the per-kernel times.  Returns (ms of the
+    clean steps, per-kernel times of the profiled pass)."""
+    stream = torch.cuda.current_stream(dev)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(nsteps):
+        s.step(U, dU, t0 + k * dt, dt)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1)
+    F.flexi_kernel_times(s.ctx, reset=True)
+    F.flexi_profile(s.ctx, True)
+    for k in range(nsteps):
+        s.step(U, dU, t0 + (nsteps + k) * dt, dt)
+    torch.cuda.synchronize(dev)
+    kt = F.flexi_kernel_times(s.ctx, reset=True)
+    F.flexi_profile(s.ctx, False)
+    return ms, kt
 
 
 def main():
@@ -262,10 +307,22 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the FP32 and adjoint extra measurements")
     ap.add_argument("--form", default="fp64", choices=["fp64", "fp32", "tf32x3", "bf16x3"],
                     help="arithmetic form of the timed workload (default: the FP64 headline)")
+    ap.add_argument("--threads", type=int, default=None, help="host threads of the reference arm (default: all)")
+    ap.add_argument("--nelem", type=int, default=16,
+                    help="elements per direction of the timed Taylor-Green mesh (16: the headline workload; "
+                         "smaller meshes for profiler captures)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         return reference_arm(args)
+    world, rank, local = dist_env()
+    cpu_line = None
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        # before any GPU work in this process: the oracle in fresh processes
+        try:
+            cpu_line = run_cpu_baseline()
+        except Exception as exc:  # pragma: no cover
+            cpu_line = {"value": None, "error": repr(exc)}
 
     import numpy as np
     import torch
@@ -275,7 +332,6 @@ def main():
     from paper_1910_02858_gb300 import build as B
     from paper_1910_02858_gb300 import flexi as F
 
-    world, rank, local = dist_env()
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -290,9 +346,12 @@ def main():
     F.lib()
 
     N = 7
-    mesh = wl.box_mesh((16, 16, 16), Ngeo=1)
+    mesh = wl.box_mesh((args.nelem,) * 3, Ngeo=1)
     x = mesh.node_coords(N, 0)
     U0 = wl.taylor_green(x)
+    workload = WORKLOAD if args.nelem == 16 else dict(
+        WORKLOAD, workload=WORKLOAD["workload"].replace("16^3", f"{args.nelem}^3"), elements=mesh.K,
+        dof=mesh.K * (N + 1) ** 3, l2="small profiling case")
     prec = {"fp64": F.FP64, "fp32": F.FP32, "tf32x3": F.FP32_TF32, "bf16x3": F.FP32_BF16}[args.form]
     cfg = SolverConfig(N=N, riemann=F.RIEMANN_HLLC, precision=prec)
     s = Solver(cfg, mesh.coords, mesh.conn, device=dev)
@@ -310,15 +369,16 @@ def main():
     F.flexi_profile(s.ctx, True)
     s.step(U.clone(), dU.clone(), 0.0, dt)
     launches_per_step = sum(c for _, c in F.flexi_kernel_times(s.ctx, reset=True).values())
+    F.flexi_profile(s.ctx, False)
 
     t = 0.0
     for _ in range(args.warmup):
         s.step(U, dU, t, dt)
         t += dt
-    F.flexi_kernel_times(s.ctx, reset=True)
     barrier()
     torch.cuda.synchronize(dev)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # the timed region: the product's launch stream, no per-launch events
     with ClockSampler(local) as clk:
         ev0.record(stream)
         for _ in range(args.steps):
@@ -328,6 +388,18 @@ def main():
         torch.cuda.synchronize(dev)
     barrier()
     ms_total = ev0.elapsed_time(ev1)
+    # per-kernel times: the same number of steps again, with the library's per-launch
+    # CUDA events (on the launching stream), timed on their own
+    F.flexi_kernel_times(s.ctx, reset=True)
+    F.flexi_profile(s.ctx, True)
+    pe0, pe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    pe0.record(stream)
+    for _ in range(args.steps):
+        s.step(U, dU, t, dt)
+        t += dt
+    pe1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_profiled = pe0.elapsed_time(pe1)
     ktimes = F.flexi_kernel_times(s.ctx, reset=True)
     F.flexi_profile(s.ctx, False)
     ms_total = max_over_ranks(ms_total, dist, dev)
@@ -387,20 +459,20 @@ def main():
     line = {"metric": METRIC, "value": pid, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if args.form == "fp64" else "f32", "data": "synthetic",
-            "config": dict(WORKLOAD, dt=dt, form=args.form),
+            "config": dict(workload, dt=dt, form=args.form),
             "clocks": clk.summary(), "gpu_launches": launches_per_step * args.steps,
             "e2e": {"value": e2e_pid, "unit": UNIT, "h2d_bytes_per_step": ubytes, "d2h_bytes_per_step": ubytes},
             "roofline": roofline, "dof_updates_per_s": dof * world / (pid * 1e-9 * dof * world) if pid else None,
             "step_algorithmic_hbm_gbs": step_bytes_gbs, "step_roofline": step_roofline, "kernels": kernels}
 
+    line["profiled_pass"] = {"steps": args.steps, "ms_per_step": ms_profiled / args.steps,
+                             "note": "per-kernel times and the roofline's launch duration come from this pass "
+                                     "(library CUDA events around every launch); value is timed without them"}
     if rank == 0 and not args.no_extras:
         line["extras"] = extras(args, s, U0, mesh, dt, dev, F, wl, Solver, SolverConfig, torch, np)
     s.close()
-    if rank == 0 and not args.no_cpu_baseline and world == 1:
-        try:
-            line["cpu_baseline"] = run_cpu_baseline()
-        except Exception as exc:  # pragma: no cover
-            line["cpu_baseline"] = {"value": None, "error": repr(exc)}
+    if cpu_line is not None:
+        line["cpu_baseline"] = cpu_line
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -440,17 +512,10 @@ def extras(args, s64, U0, mesh, dt, dev, F, wl, Solver, SolverConfig, torch, np)
                 s.step(U, dU, 0.0, dt)
             U = torch.tensor(U0, device=dev, dtype=torch.float32)
             dU.zero_()
-            F.flexi_profile(s.ctx, True)
-            torch.cuda.synchronize(dev)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            for k in range(nsteps):
-                s.step(U, dU, k * dt, dt)
-            e1.record()
-            torch.cuda.synchronize(dev)
-            ms = e0.elapsed_time(e1)
-            kt = F.flexi_kernel_times(s.ctx, reset=True)
-            F.flexi_profile(s.ctx, False)
+            ms, kt = timed_steps(s, U, dU, dt, nsteps, F, torch, dev)
+            # the error against FP64 is taken after the first nsteps steps (as the FP64 run)
+            U = torch.tensor(U0, device=dev, dtype=torch.float32)
+            s.run(U, nsteps, dt)
             dof = s.query(F.Q_DOF)
             n = 8
             bytes_stage = (46.0 + 117.0 * 3.0 / n) * 4 * dof
@@ -471,6 +536,10 @@ def extras(args, s64, U0, mesh, dt, dev, F, wl, Solver, SolverConfig, torch, np)
         out["lobatto"] = lobatto_pid(mesh, dt, dev, F, wl, Solver, SolverConfig, torch)
     except Exception as exc:
         out["lobatto"] = {"error": repr(exc)}
+    try:
+        out["c4_curved_24^3_N7"] = c4_curved_pid(dev, F, wl, Solver, SolverConfig, torch)
+    except Exception as exc:
+        out["c4_curved_24^3_N7"] = {"error": repr(exc)}
     try:
         out["c3_32^3_N5"] = c3_forms_pid(dev, F, wl, Solver, SolverConfig, torch)
     except Exception as exc:
@@ -510,24 +579,65 @@ def lobatto_pid(mesh, dt, dev, F, wl, Solver, SolverConfig, torch):
             dU = torch.zeros_like(U)
             for _ in range(3):
                 s.step(U, dU, 0.0, dt)
-            torch.cuda.synchronize(dev)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            for k in range(10):
-                s.step(U, dU, k * dt, dt)
-            e1.record()
-            torch.cuda.synchronize(dev)
-            ms = e0.elapsed_time(e1)
-            F.flexi_profile(s.ctx, True)
-            for k in range(2):
-                s.step(U, dU, k * dt, dt)
-            torch.cuda.synchronize(dev)
-            kt = F.flexi_kernel_times(s.ctx, reset=True)
-            F.flexi_profile(s.ctx, False)
+            ms, kt = timed_steps(s, U, dU, dt, 10, F, torch, dev)
             res[name] = {"pid": ms * 1e6 / (10 * NSTAGES * s.query(F.Q_DOF)), "steps": 10,
                          "lift_vol_ms_per_launch": kt["lift_vol"][0] / max(kt["lift_vol"][1], 1)}
         finally:
             s.close()
+    return res
+
+
+def c4_curved_pid(dev, F, wl, Solver, SolverConfig, torch):
+    """The curved-mesh workload: [-1, 1]^3, 24^3 elements mapped by
+    x_i = xi_i + 0.1 prod_j sin(pi xi_j), N = Ngeo = 7 Gauss, curl-form metrics,
+    HLLC, BR1, Dirichlet (exact-state) boundaries on all six sides (7,077,888 DOF).
+    (a) free stream rho = 1, u = (0.3, 0.2, 0.1), p = 1/gamma (operator independent
+    of t: the exact state is constant); (b) the manufactured solution with its
+    source term (time-dependent boundary state and source).  FP64 and FP32: PID,
+    whole-step roofline fraction, the lifting/volume kernel's time and share, and
+    for (a) the largest deviation from the free stream after the steps."""
+    mesh = wl.box_mesh((24, 24, 24), lo=(-1.0,) * 3, hi=(1.0,) * 3, Ngeo=7, mapping="sine", periodic=(False,) * 3)
+    N, nsteps = 7, 10
+    x = mesh.node_coords(N, 0)
+    res = {}
+    for case, U0, bc, src in (("freestream", wl.freestream(x), F.EXACT_FREESTREAM, False),
+                              ("manufactured", wl.manufactured(x, 0.0), F.EXACT_MANUFACTURED, True)):
+        for name, prec in (("fp64", F.FP64), ("fp32", F.FP32)):
+            s = Solver(SolverConfig(N=N, Ngeo=N, riemann=F.RIEMANN_HLLC, precision=prec, bc_exact=bc, source=src),
+                       mesh.coords, mesh.conn, device=dev)
+            try:
+                U = torch.tensor(U0, device=dev, dtype=s.dtype)
+                dt = s.reduce(U)["dt_max"]
+                dU = torch.zeros_like(U)
+                for k in range(3):
+                    s.step(U, dU, k * dt, dt)
+                U = torch.tensor(U0, device=dev, dtype=s.dtype)
+                dU.zero_()
+                ms, kt = timed_steps(s, U, dU, dt, nsteps, F, torch, dev)
+                dof = s.query(F.Q_DOF)
+                pid = ms * 1e6 / (nsteps * NSTAGES * dof)
+                fpk = FP64_PEAK_TFLOPS if prec == F.FP64 else FP32_PEAK_TFLOPS
+                floor = max(s.query(F.Q_BYTES_PER_STAGE) / dof / peaks().get("hbm_gbs", 6800.0),
+                            s.query(F.Q_FLOPS_PER_STAGE) / dof / (fpk * 1e3))
+                tot = sum(v[0] for v in kt.values())
+                lv = kt["lift_vol"][0] / max(kt["lift_vol"][1], 1)
+                row = {"dof": dof, "dt": dt, "steps": nsteps, "pid": pid, "step_roofline_frac": floor / pid,
+                       "floor_ns": floor, "lift_vol_ms_per_launch": lv,
+                       "lift_vol_share": kt["lift_vol"][0] / tot if tot > 0 else None}
+                if prec == F.FP64:
+                    row["lift_vol_alu_frac"] = (algorithmic_per_dof(N + 1, 8)[2] * dof / (lv * 1e-3) / 1e12
+                                                / FP64_PEAK_TFLOPS)
+                else:
+                    row["lift_vol_hbm_frac"] = (algorithmic_per_dof(N + 1, 4)[1] * dof / (lv * 1e-3) / 1e9
+                                                / peaks().get("hbm_gbs", 6800.0))
+                if case == "freestream":
+                    # 2 * nsteps steps were taken from U0 (timed + profiled pass)
+                    U0d = torch.tensor(U0, device=dev, dtype=s.dtype)
+                    row["freestream_max_rel_dev"] = float(((U - U0d).abs().amax(dim=(0, 2, 3, 4))
+                                                           / U0d.abs().amax(dim=(0, 2, 3, 4))).max())
+                res[f"{case}_{name}"] = row
+            finally:
+                s.close()
     return res
 
 
@@ -640,20 +750,7 @@ def mortar_pid(dt, dev, F, wl, Solver, SolverConfig, torch):
         dtm = 0.5 * dt  # the fine half has half the element width
         for _ in range(3):
             s.step(U, dU, 0.0, dtm)
-        torch.cuda.synchronize(dev)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for k in range(10):
-            s.step(U, dU, k * dtm, dtm)
-        e1.record()
-        torch.cuda.synchronize(dev)
-        ms = e0.elapsed_time(e1)
-        F.flexi_profile(s.ctx, True)
-        for k in range(2):
-            s.step(U, dU, k * dtm, dtm)
-        torch.cuda.synchronize(dev)
-        kt = F.flexi_kernel_times(s.ctx, reset=True)
-        F.flexi_profile(s.ctx, False)
+        ms, kt = timed_steps(s, U, dU, dtm, 10, F, torch, dev)
         tot = sum(v[0] for v in kt.values())
         return {"elements": m.K, "mortars": int(len(m.mortars)), "pid": ms * 1e6 / (10 * NSTAGES * s.query(F.Q_DOF)),
                 "steps": 10, "mortar_kernel_share": kt["other"][0] / tot if tot > 0 else None}
