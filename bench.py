@@ -50,7 +50,7 @@ def peaks():
 # capture time; reported only while the sources are unchanged (else null).
 KERNEL_SOURCES = ["paper_1910_02858_gb300/csrc/k_dg.cuh", "paper_1910_02858_gb300/csrc/dg_common.cuh",
                   "paper_1910_02858_gb300/csrc/k_tc.cuh"]
-NCU_TRAFFIC = {("fp64", "ee20b777e1ed5af9"): 575187968, ("fp32", "ee20b777e1ed5af9"): 265205248}
+NCU_TRAFFIC = {("fp64", "fe9c8b798b0d4267"): 573841408, ("fp32", "fe9c8b798b0d4267"): 266458112}
 
 
 def kernel_source_hash(texts=None) -> str:
@@ -728,7 +728,14 @@ def small_cases_pid(dev, F, wl, Solver, SolverConfig, torch):
                 e1.record()
                 torch.cuda.synchronize(dev)
                 out[mode] = e0.elapsed_time(e1) * 1e6 / (200 * NSTAGES * dof)
-            res[label] = {"dof": dof, "pid_launches": out["launches"], "pid_graph": out["graph"]}
+            F.flexi_kernel_times(s.ctx, reset=True)
+            F.flexi_profile(s.ctx, True)
+            s.run(U, 20, 1e-4, graph=False)
+            torch.cuda.synchronize(dev)
+            kt = F.flexi_kernel_times(s.ctx, reset=True)
+            F.flexi_profile(s.ctx, False)
+            res[label] = {"dof": dof, "pid_launches": out["launches"], "pid_graph": out["graph"],
+                          "us_per_launch": {k: v[0] / v[1] * 1e3 for k, v in kt.items() if v[1]}}
         finally:
             s.close()
     return res
@@ -762,15 +769,20 @@ def adjoint_ratio(dev, F, wl, Solver, SolverConfig, torch):
     """Cost of dJ/dU0 (checkpointed forward + recompute + reverse sweep) over the
     cost of the plain forward run, on the adjoint workload: Taylor-Green Re = 400,
     8^3, N = 5, Roe with smoothed |lambda|, 40 steps of dt = 1e-3, checkpoints
-    every 20 steps; and the per-step ratio at N = 7, 16^3."""
+    every 20 steps; the per-step ratio at N = 7, 16^3; and the same workload on
+    Gauss-Lobatto nodes with the split-form volume integral (kinetic-energy-preserving
+    and entropy-conservative two-point fluxes)."""
     from paper_1910_02858_gb300.adjoint import final_state
 
     res = {}
-    for label, nel, N, nsteps in (("c5_8^3_N5_40steps", 8, 5, 40), ("16^3_N7_10steps", 16, 7, 10)):
+    for label, nel, N, nsteps, nt, split in (("c5_8^3_N5_40steps", 8, 5, 40, 0, F.SPLIT_STANDARD),
+                                             ("16^3_N7_10steps", 16, 7, 10, 0, F.SPLIT_STANDARD),
+                                             ("c5_lgl_split_kep", 8, 5, 40, 1, F.SPLIT_KEP),
+                                             ("c5_lgl_split_ec", 8, 5, 40, 1, F.SPLIT_EC)):
         mesh = wl.box_mesh((nel,) * 3, Ngeo=1)
-        s = Solver(SolverConfig(N=N, riemann=F.RIEMANN_ROE_SMOOTH, mu=1 / 400.0, adjoint=True), mesh.coords, mesh.conn,
-                   device=dev)
-        U0 = torch.tensor(wl.taylor_green(mesh.node_coords(N, 0)), device=dev)
+        s = Solver(SolverConfig(N=N, node_type=nt, riemann=F.RIEMANN_ROE_SMOOTH, mu=1 / 400.0, adjoint=True,
+                                split_form=split), mesh.coords, mesh.conn, device=dev)
+        U0 = torch.tensor(wl.taylor_green(mesh.node_coords(N, nt)), device=dev)
         dt = 1e-3
         lam = torch.randn_like(U0)
 

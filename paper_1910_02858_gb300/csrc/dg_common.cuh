@@ -130,9 +130,9 @@ __device__ __forceinline__ void flux_total(const real U[NV], const real W[NV], c
   F[4] = ud * (U[4] + p) - fv4;
 }
 
-// normal viscous flux F^v . n
+// normal viscous flux F^v . n, with ir = 1 / rho of the state
 template <typename real>
-__device__ __forceinline__ void visc_normal(const real W[NV], const real G[15], const real n[3],
+__device__ __forceinline__ void visc_normal(const real W[NV], const real ir, const real G[15], const real n[3],
                                             const Phys<real>& ph, real f[NV]) {
   const real div = G[0 * 5 + 1] + G[1 * 5 + 2] + G[2 * 5 + 3];
   real tn[3];
@@ -143,7 +143,6 @@ __device__ __forceinline__ void visc_normal(const real W[NV], const real G[15], 
     for (int d = 0; d < 3; ++d) s += (G[d * 5 + 1 + c] + G[c * 5 + 1 + d]) * n[d];
     tn[c] = ph.mu * (s - real(2.0 / 3.0) * div * n[c]);
   }
-  const real ir = real(1) / W[0];
   const real pir = W[4] * ir;
   real dTn = real(0);
 #pragma unroll
@@ -156,6 +155,12 @@ __device__ __forceinline__ void visc_normal(const real W[NV], const real G[15], 
 }
 
 template <typename real>
+__device__ __forceinline__ void visc_normal(const real W[NV], const real G[15], const real n[3],
+                                            const Phys<real>& ph, real f[NV]) {
+  visc_normal(W, real(1) / W[0], G, n, ph, f);
+}
+
+template <typename real>
 __device__ __forceinline__ real dg_sqrt(real x);
 template <>
 __device__ __forceinline__ double dg_sqrt<double>(double x) { return sqrt(x); }
@@ -164,6 +169,20 @@ __device__ __forceinline__ float dg_sqrt<float>(float x) { return sqrtf(x); }
 
 template <typename real>
 __device__ __forceinline__ real dg_abs(real x) { return x < real(0) ? -x : x; }
+
+// a * b + c in one rounding (one FP64 pipe slot for two flops in the FP64 form;
+// a sum written as acc + (a0 b0 + a1 b1) costs a multiply, a fused multiply-add
+// and an add instead of two fused multiply-adds)
+__device__ __forceinline__ double dg_fma(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float dg_fma(float a, float b, float c) { return fmaf(a, b, c); }
+
+// -x when flag is set, by flipping the sign bit on the integer pipe (no FP64 multiply)
+__device__ __forceinline__ double dg_neg_if(double x, bool flag) {
+  return __longlong_as_double(__double_as_longlong(x) ^ ((long long)flag << 63));
+}
+__device__ __forceinline__ float dg_neg_if(float x, bool flag) {
+  return __int_as_float(__float_as_int(x) ^ ((int)flag << 31));
+}
 
 // Euler normal flux from primitives
 template <typename real>
@@ -176,26 +195,28 @@ __device__ __forceinline__ void euler_normal(const real W[NV], real E, real un, 
   F[4] = (E + W[4]) * un;
 }
 
-// HLLC (Toro) with Einfeldt/Davis wave speeds, frame-free form
+// HLLC (Toro) with Einfeldt/Davis wave speeds, frame-free form; irL, irR = 1 / rho.
+// Roe averages with the weights sqrt(rho_L), sqrt(rho_R) written with their ratio
+// r = sqrt(rho_R / rho_L): (a_L + r a_R) / (1 + r) (one square root, one division);
+// the star-state factors mK / (S - S*) and p / mK share one division.
 template <typename real>
-__device__ __forceinline__ void riemann_hllc(const real WL[NV], const real WR[NV], const real n[3],
-                                             const Phys<real>& ph, real f[NV]) {
+__device__ __forceinline__ void riemann_hllc(const real WL[NV], const real WR[NV], const real irL, const real irR,
+                                             const real n[3], const Phys<real>& ph, real f[NV]) {
   const real q2L = WL[1] * WL[1] + WL[2] * WL[2] + WL[3] * WL[3];
   const real q2R = WR[1] * WR[1] + WR[2] * WR[2] + WR[3] * WR[3];
   const real EL = WL[4] * ph.inv_gm1 + real(0.5) * WL[0] * q2L;
   const real ER = WR[4] * ph.inv_gm1 + real(0.5) * WR[0] * q2R;
   const real uL = WL[1] * n[0] + WL[2] * n[1] + WL[3] * n[2];
   const real uR = WR[1] * n[0] + WR[2] * n[1] + WR[3] * n[2];
-  const real irL = real(1) / WL[0], irR = real(1) / WR[0];
   const real cL = dg_sqrt(ph.gamma * WL[4] * irL);
   const real cR = dg_sqrt(ph.gamma * WR[4] * irR);
-  const real sL = dg_sqrt(WL[0]), sR = dg_sqrt(WR[0]);
-  const real iws = real(1) / (sL + sR);
+  const real r = dg_sqrt(WR[0] * irL);
+  const real iw = real(1) / (real(1) + r);
   const real HL = (EL + WL[4]) * irL, HR = (ER + WR[4]) * irR;
   real vel[3];
 #pragma unroll
-  for (int c = 0; c < 3; ++c) vel[c] = (sL * WL[1 + c] + sR * WR[1 + c]) * iws;
-  const real H = (sL * HL + sR * HR) * iws;
+  for (int c = 0; c < 3; ++c) vel[c] = (WL[1 + c] + r * WR[1 + c]) * iw;
+  const real H = (HL + r * HR) * iw;
   const real c = dg_sqrt(ph.gm1 * (H - real(0.5) * (vel[0] * vel[0] + vel[1] * vel[1] + vel[2] * vel[2])));
   const real un = vel[0] * n[0] + vel[1] * n[1] + vel[2] * n[2];
   const real SL = fmin(uL - cL, un - c);
@@ -211,14 +232,19 @@ __device__ __forceinline__ void riemann_hllc(const real WL[NV], const real WR[NV
   const real mL = WL[0] * (SL - uL), mR = WR[0] * (SR - uR);
   const real Ss = (WR[4] - WL[4] + mL * uL - mR * uR) / (mL - mR);
   const bool left = Ss >= real(0);
-  const real* W = left ? WL : WR;
+  real W[NV];  // the upwind state, selected by value (a pointer select would force the arrays to memory)
+#pragma unroll
+  for (int v = 0; v < NV; ++v) W[v] = left ? WL[v] : WR[v];
   const real E = left ? EL : ER;
   const real uK = left ? uL : uR;
   const real S = left ? SL : SR;
   const real mK = left ? mL : mR;
+  const real irK = left ? irL : irR;
   euler_normal(W, E, uK, n, f);
-  // star state: fac (1, S* n + v_t, E/rho + (S*-u)(S* + p/(rho(S-u))))
-  const real fac = mK / (S - Ss);
+  // star state: fac (1, S* n + v_t, E/rho + (S*-u)(S* + p/(rho(S-u)))), fac = mK / (S - S*)
+  const real dS = S - Ss;
+  const real q = real(1) / (mK * dS);
+  const real fac = mK * mK * q;
   const real U0 = W[0];
   f[0] += S * (fac - U0);
 #pragma unroll
@@ -226,8 +252,14 @@ __device__ __forceinline__ void riemann_hllc(const real WL[NV], const real WR[NV
     const real vt = W[1 + c] - uK * n[c];
     f[1 + c] += S * (fac * (vt + Ss * n[c]) - U0 * W[1 + c]);
   }
-  const real Estar = fac * (E / U0 + (Ss - uK) * (Ss + W[4] / mK));
+  const real Estar = fac * (E * irK + (Ss - uK) * (Ss + W[4] * dS * q));
   f[4] += S * (Estar - E);
+}
+
+template <typename real>
+__device__ __forceinline__ void riemann_hllc(const real WL[NV], const real WR[NV], const real n[3],
+                                             const Phys<real>& ph, real f[NV]) {
+  riemann_hllc(WL, WR, real(1) / WL[0], real(1) / WR[0], n, ph, f);
 }
 
 // Roe flux (5-wave, frame-free); smooth != 0: Harten-type smoothing of |lambda|
@@ -364,6 +396,21 @@ __device__ __forceinline__ void riemann_ec(const real WL[NV], const real WR[NV],
           real(0.5) * WR[0] / WR[4], uR[0] * uR[0] + uR[1] * uR[1] + uR[2] * uR[2], n, ph, f);
 }
 
+// numerical flux of a compile-time kind RS (FLEXI_RIEMANN_*: 0 Roe and 2 smoothed Roe
+// both take the Roe branch, smoothing from ph), with irL, irR = 1 / rho
+template <int RS, typename real>
+__device__ __forceinline__ void riemann_kind(const real WL[NV], const real WR[NV], const real irL, const real irR,
+                                             const real n[3], const Phys<real>& ph, real f[NV]) {
+  if constexpr (RS == 1)
+    riemann_hllc(WL, WR, irL, irR, n, ph, f);
+  else if constexpr (RS == 3)
+    riemann_rusanov(WL, WR, n, ph, f);
+  else if constexpr (RS == 4)
+    riemann_ec(WL, WR, n, ph, f);
+  else
+    riemann_roe(WL, WR, n, ph, ph.riemann == 2, f);
+}
+
 template <typename real>
 __device__ __forceinline__ void riemann(const real WL[NV], const real WR[NV], const real n[3],
                                         const Phys<real>& ph, real f[NV]) {
@@ -429,6 +476,25 @@ __device__ __forceinline__ void manufactured_source(const double x[3], double t,
   S[0] = dr;
   S[1] = S[2] = S[3] = dr + dpx;
   S[4] = 2.0 * rho * dr + 3.0 * dpx + 3.0 * (mu * gamma / Pr) * pi * pi * A * s;
+}
+
+// The same source term for the FP32 forms: the phase x + y + z - 2t is formed and
+// reduced modulo 2 in FP64 (exact reduction of sin(pi r), cos(pi r) to r in [0, 2)),
+// sin(pi r) and cos(pi r) come from sincospif, and the rest is FP32 arithmetic,
+// so that the term costs a few FP64 operations per node instead of an FP64 sincos.
+__device__ __forceinline__ void manufactured_source_f32(const double x[3], double t, float gamma, float mu,
+                                                        float Pr, float S[NV]) {
+  const float A = 0.1f, pi = 3.14159265358979323846f;
+  const double ph = x[0] + x[1] + x[2] - 2.0 * t;
+  const double r = ph - 2.0 * floor(0.5 * ph);
+  float s, c;
+  sincospif((float)r, &s, &c);
+  const float rho = 2.0f + A * s;
+  const float dr = pi * A * c;
+  const float dpx = (gamma - 1.0f) * (2.0f * rho - 1.5f) * dr;
+  S[0] = dr;
+  S[1] = S[2] = S[3] = dr + dpx;
+  S[4] = 2.0f * rho * dr + 3.0f * dpx + 3.0f * (mu * gamma / Pr) * pi * pi * A * s;
 }
 
 }  // namespace flexi

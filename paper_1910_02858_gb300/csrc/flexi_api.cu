@@ -545,6 +545,7 @@ flexi_status mesh_init_impl(flexi_ctx* c, const flexi_params* p, int K, const do
 
   // ---- arithmetic-form copies and scratch
   c->m.K = K; c->m.S = S; c->m.nBC = c->nBC; c->m.N = N; c->m.n = n;
+  CK(cudaDeviceGetAttribute(&c->m.nsm, cudaDevAttrMultiProcessorCount, c->device));
   c->m.Sface = S - M;
   c->m.vbase = vbase;
   c->m.nV = nV;

@@ -499,9 +499,13 @@ __device__ __forceinline__ void lift_vol_body(
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
         const int o = (v * 3 + d) * n2;
-        acc[v] += c0 * Qe[0 * 15 * n2 + o + pq0] + c1 * Qe[1 * 15 * n2 + o + pq0];
-        acc[v] += c2 * Qe[2 * 15 * n2 + o + pq1] + c3 * Qe[3 * 15 * n2 + o + pq1];
-        acc[v] += c4 * Qe[4 * 15 * n2 + o + pq2] + c5 * Qe[5 * 15 * n2 + o + pq2];
+        real a = acc[v];
+        a = dg_fma(c0, Qe[0 * 15 * n2 + o + pq0], a);
+        a = dg_fma(c1, Qe[1 * 15 * n2 + o + pq0], a);
+        a = dg_fma(c2, Qe[2 * 15 * n2 + o + pq1], a);
+        a = dg_fma(c3, Qe[3 * 15 * n2 + o + pq1], a);
+        a = dg_fma(c4, Qe[4 * 15 * n2 + o + pq2], a);
+        acc[v] = dg_fma(c5, Qe[5 * 15 * n2 + o + pq2], a);
       }
     } else if constexpr (!kLines) {  // Gauss-Lobatto: only nodes on a face receive its term
 #pragma unroll
@@ -918,7 +922,9 @@ constexpr size_t lift_vol_smem() {
 // ---------------------------------------------------------------------------
 // a5: numerical flux on every side (master normal)
 // ---------------------------------------------------------------------------
-template <typename real, int n>
+// RS: the Riemann solver (FLEXI_RIEMANN_*; 0 serves Roe and smoothed Roe), a template
+// parameter so that each kernel holds the registers of its own solver only
+template <typename real, int n, int RS>
 __global__ void __launch_bounds__(128, sizeof(real) == 4 ? 8 : 1) k_face(const real* __restrict__ Wf, const real* __restrict__ Gf,
                                               const real* __restrict__ fgeo, real* __restrict__ Ff, int S, int nBC,
                                               Phys<real> ph) {
@@ -942,9 +948,10 @@ __global__ void __launch_bounds__(128, sizeof(real) == 4 ? 8 : 1) k_face(const r
   for (int d = 0; d < 3; ++d) nv[d] = fgeo[((size_t)side * 4 + d) * n2 + pq];
   const real sa = fgeo[((size_t)side * 4 + 3) * n2 + pq];
   real f[NV], fl[NV], fr[NV];
-  riemann(WL, WR, nv, ph, f);
-  visc_normal(WL, GL, nv, ph, fl);
-  visc_normal(WR, GR, nv, ph, fr);
+  const real irL = real(1) / WL[0], irR = real(1) / WR[0];  // shared by the Riemann and viscous fluxes
+  riemann_kind<RS>(WL, WR, irL, irR, nv, ph, f);
+  visc_normal(WL, irL, GL, nv, ph, fl);
+  visc_normal(WR, irR, GR, nv, ph, fr);
 #pragma unroll
   for (int v = 0; v < NV; ++v) Ff[((size_t)side * NV + v) * n2 + pq] = (f[v] - real(0.5) * (fl[v] + fr[v])) * sa;
 }
@@ -995,12 +1002,13 @@ __global__ void __launch_bounds__(Cfg<n>::T, (sizeof(real) == 4 && Cfg<n>::T == 
     if (e0 + el2 >= K) continue;
     const int es = sES[el2 * 6 + s];
     const int mpq = orient_pq(es_orient(es), n - 1, pq % n, pq / n);
-    const real sg = es_slave(es) ? real(-1) : real(1);
     const real* src_f = Ff + ((size_t)es_side(es) * NV) * n2 + mpq;
+    const bool slave = es_slave(es);  // the slave side takes -f* s_hat
 #pragma unroll
-    for (int v = 0; v < NV; ++v) sF[((el2 * 6 + s) * NV + v) * n2 + pq] = sg * src_f[v * n2];
+    for (int v = 0; v < NV; ++v) sF[((el2 * 6 + s) * NV + v) * n2 + pq] = dg_neg_if(src_f[v * n2], slave);
   }
   __syncthreads();
+  // ut = U_t (MODE 0) or dt U_t (MODE 1: dt folded into the -1/J factor)
   real ut[NV];
   if (valid) {
     const real* lhm = sOp + n2 + 2 * n;
@@ -1008,30 +1016,43 @@ __global__ void __launch_bounds__(Cfg<n>::T, (sizeof(real) == 4 && Cfg<n>::T == 
     const real c0 = lhm[i], c1 = lhp[i], c2 = lhm[j], c3 = lhp[j], c4 = lhm[k], c5 = lhp[k];
     const int pq0 = j + n * k, pq1 = i + n * k, pq2 = i + n * j;
     const real* Fe = sF + el * 6 * NV * n2;
+    const real scale = MODE == 1 ? -(rk.dt * sj) : -sj;
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       real s = vtv[v];
       if (LGL) {  // Gauss-Lobatto: only nodes on a face receive its flux
-        if (i == 0) s += c0 * Fe[(0 * NV + v) * n2 + pq0];
-        if (i == n - 1) s += c1 * Fe[(1 * NV + v) * n2 + pq0];
-        if (j == 0) s += c2 * Fe[(2 * NV + v) * n2 + pq1];
-        if (j == n - 1) s += c3 * Fe[(3 * NV + v) * n2 + pq1];
-        if (k == 0) s += c4 * Fe[(4 * NV + v) * n2 + pq2];
-        if (k == n - 1) s += c5 * Fe[(5 * NV + v) * n2 + pq2];
+        if (i == 0) s = dg_fma(c0, Fe[(0 * NV + v) * n2 + pq0], s);
+        if (i == n - 1) s = dg_fma(c1, Fe[(1 * NV + v) * n2 + pq0], s);
+        if (j == 0) s = dg_fma(c2, Fe[(2 * NV + v) * n2 + pq1], s);
+        if (j == n - 1) s = dg_fma(c3, Fe[(3 * NV + v) * n2 + pq1], s);
+        if (k == 0) s = dg_fma(c4, Fe[(4 * NV + v) * n2 + pq2], s);
+        if (k == n - 1) s = dg_fma(c5, Fe[(5 * NV + v) * n2 + pq2], s);
       } else {
-        s += c0 * Fe[(0 * NV + v) * n2 + pq0] + c1 * Fe[(1 * NV + v) * n2 + pq0];
-        s += c2 * Fe[(2 * NV + v) * n2 + pq1] + c3 * Fe[(3 * NV + v) * n2 + pq1];
-        s += c4 * Fe[(4 * NV + v) * n2 + pq2] + c5 * Fe[(5 * NV + v) * n2 + pq2];
+        s = dg_fma(c0, Fe[(0 * NV + v) * n2 + pq0], s);
+        s = dg_fma(c1, Fe[(1 * NV + v) * n2 + pq0], s);
+        s = dg_fma(c2, Fe[(2 * NV + v) * n2 + pq1], s);
+        s = dg_fma(c3, Fe[(3 * NV + v) * n2 + pq1], s);
+        s = dg_fma(c4, Fe[(4 * NV + v) * n2 + pq2], s);
+        s = dg_fma(c5, Fe[(5 * NV + v) * n2 + pq2], s);
       }
-      ut[v] = -s * sj;
+      ut[v] = s * scale;
     }
     if (src.on) {
-      double x[3], Sv[NV];
+      double x[3];
 #pragma unroll
       for (int c = 0; c < 3; ++c) x[c] = xsol[((size_t)e * 3 + c) * n3 + node];
-      manufactured_source(x, t, src.gamma, src.mu, src.Pr, Sv);
+      const real sdt = MODE == 1 ? rk.dt : real(1);
+      if constexpr (sizeof(real) == 4) {
+        float Sv[NV];
+        manufactured_source_f32(x, t, (float)src.gamma, (float)src.mu, (float)src.Pr, Sv);
 #pragma unroll
-      for (int v = 0; v < NV; ++v) ut[v] += (real)Sv[v];
+        for (int v = 0; v < NV; ++v) ut[v] = dg_fma(sdt, Sv[v], ut[v]);
+      } else {
+        double Sv[NV];
+        manufactured_source(x, t, src.gamma, src.mu, src.Pr, Sv);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) ut[v] = dg_fma(sdt, (real)Sv[v], ut[v]);
+      }
     }
   }
   if (MODE == 0) {
@@ -1045,8 +1066,8 @@ __global__ void __launch_bounds__(Cfg<n>::T, (sizeof(real) == 4 && Cfg<n>::T == 
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
         const size_t g = ((size_t)e * NV + v) * n3 + node;
-        const real du = rk.A * vdU[v] + rk.dt * ut[v];
-        const real un = vU[v] + rk.B * du;
+        const real du = dg_fma(rk.A, vdU[v], ut[v]);  // A dU + dt U_t
+        const real un = dg_fma(rk.B, du, vU[v]);
         dU[g] = du;
         U[g] = un;
         sU[(el * NV + v) * C::n3p + pidx<n>(i, j, k)] = un;
@@ -1156,8 +1177,28 @@ cudaError_t launch_lift_vol(const DevMesh& m, const real* U, const Ops<real>& op
 template <typename real>
 cudaError_t launch_face(const DevMesh& m, const Phys<real>& ph, cudaStream_t st) {
   const int tot = m.Sface * m.n * m.n;  // big sides of mortars get their flux by projection
-  FLEXI_DISPATCH_N(m.n, (k_face<real, NN><<<(tot + 127) / 128, 128, 0, st>>>(
-                            (const real*)m.Wf, (const real*)m.Gf, (const real*)m.fgeo, (real*)m.Ff, m.S, m.nBC, ph)));
+  if (tot == 0) return cudaSuccess;
+  // one warp per CTA when 128-thread CTAs would leave SMs idle (small meshes: the
+  // FP64 flux is pipe-bound per SM, so spreading the face nodes over more SMs pays)
+  const int TB = (tot + 127) / 128 >= 2 * m.nsm ? 128 : 32;
+  switch (ph.riemann) {
+    case 1:
+      FLEXI_DISPATCH_N(m.n, (k_face<real, NN, 1><<<(tot + TB - 1) / TB, TB, 0, st>>>(
+                                (const real*)m.Wf, (const real*)m.Gf, (const real*)m.fgeo, (real*)m.Ff, m.S, m.nBC, ph)));
+      break;
+    case 3:
+      FLEXI_DISPATCH_N(m.n, (k_face<real, NN, 3><<<(tot + TB - 1) / TB, TB, 0, st>>>(
+                                (const real*)m.Wf, (const real*)m.Gf, (const real*)m.fgeo, (real*)m.Ff, m.S, m.nBC, ph)));
+      break;
+    case 4:
+      FLEXI_DISPATCH_N(m.n, (k_face<real, NN, 4><<<(tot + TB - 1) / TB, TB, 0, st>>>(
+                                (const real*)m.Wf, (const real*)m.Gf, (const real*)m.fgeo, (real*)m.Ff, m.S, m.nBC, ph)));
+      break;
+    default:  // Roe (0) and smoothed Roe (2)
+      FLEXI_DISPATCH_N(m.n, (k_face<real, NN, 0><<<(tot + TB - 1) / TB, TB, 0, st>>>(
+                                (const real*)m.Wf, (const real*)m.Gf, (const real*)m.fgeo, (real*)m.Ff, m.S, m.nBC, ph)));
+      break;
+  }
   return cudaGetLastError();
 }
 

@@ -28,6 +28,7 @@ cudaError_t ensure_dynamic_smem(Kernel* kernel, size_t smem, std::atomic<unsigne
 // Device-resident mesh, geometry and scratch of one context (type-erased).
 struct DevMesh {
   int K = 0, S = 0, nBC = 0, N = 0, n = 0;
+  int nsm = 1;                 // streaming multiprocessors of the device (launch shapes of small meshes)
   int sweep_mode = 0;          // 0 CUDA-core line sweeps, 1 TF32 and 2 BF16 3-term split mma
   int lgl = 0;                 // 1: Gauss-Lobatto nodes (face terms only at face nodes)
   int split = 0;               // split-form volume integral: 1 kinetic-energy-preserving, 2 entropy-conservative flux

@@ -75,3 +75,25 @@ def test_c3_fp32_forms_100_steps_vs_fp64():
         assert max(errs[form]) < 1e-5, errs
         assert errs[form + "_ke"] < 1e-5, errs
         assert errs[form + "_rate"] < 2e-3, errs
+
+
+@pytest.mark.parametrize("N", [3, 7])
+def test_rhs_fp32_manufactured_source_curved(N):
+    """C4b shape in the FP32 form: curved mesh, exact-state (Dirichlet) sides and the
+    manufactured solution's source term (evaluated in FP32 after an FP64 phase
+    reduction), at a time where the phase is not small; FP32 tolerance as above."""
+    mesh = wl.box_mesh((2, 3, 2), lo=(-1,) * 3, hi=(1,) * 3, Ngeo=N, mapping="sine", periodic=(False,) * 3,
+                       reorient_seed=N)
+    sk = dict(N=N, Ngeo=N, riemann=1, bc_exact=2, source=True, precision=1)
+    s = _solver(sk, mesh)
+    dg = _oracle(sk, mesh)
+    t = 0.37
+    U0 = wl.manufactured(mesh.node_coords(N, 0), t)
+    Ut = s.rhs(torch.tensor(U0, device=DEV, dtype=torch.float32), t)
+    ref, parts = dg.rhs(torch.tensor(U0), t, parts=True)
+    scale = (ref.abs() + (parts["vol"] / dg.geo.J.unsqueeze(1)).abs()).transpose(0, 1).reshape(5, -1).norm(dim=1)
+    sig = rounding_sensitivity(dg, torch.tensor(U0), t, mesh=mesh) * 2.0 ** 29
+    d = (Ut.double().cpu() - ref).transpose(0, 1).reshape(5, -1).norm(dim=1)
+    tol = torch.maximum(3e-6 * scale, 20 * sig)
+    s.close()
+    assert bool((d <= tol).all()), (d.tolist(), tol.tolist())
