@@ -424,6 +424,34 @@ __device__ __forceinline__ void split_pair_vjp(const real Wx[NV], const real Wa[
   }
 }
 
+// Pirozzoli's pair flux reversed by hand: lamWx += d/dW_x (w . 2F#(W_x, W_a)).  With the
+// pair sums rs, s (velocity), ps, Hs and j = Jx + Ja, m = rs (s . j) / 8 and
+// w . 2F# = m A + (ps / 2) (w_1..3 . j), A = 2 w_0 + w_1..3 . s + w_4 Hs, so the partials
+// are d/drs = A (s . j) / 8, d/ds = A rs j / 8 + m w_1..3, d/dps = (w_1..3 . j) / 2 and
+// d/dHs = m w_4, carried to W_x through H_x = gamma/(gamma-1) p/rho + |u|^2/2
+// (dH/drho = dHdr, dH/du = u, dH/dp = dHdp, given per node).  both: W_a is W_x (the
+// diagonal pair), whose gradient is twice the one-sided one (F# is symmetric).
+template <typename real>
+__device__ __forceinline__ void kep_pair_vjp(const real Wx[NV], real Hx, real dHdr, real dHdp, const real Wa[NV],
+                                             real Ha, const real Jx[3], const real Ja[3], const real w[NV], bool both,
+                                             real lamWx[NV]) {
+  const real rs = Wx[0] + Wa[0], s0 = Wx[1] + Wa[1], s1 = Wx[2] + Wa[2], s2 = Wx[3] + Wa[3];
+  const real j0 = Jx[0] + Ja[0], j1 = Jx[1] + Ja[1], j2 = Jx[2] + Ja[2];
+  const real Hs = Hx + Ha;
+  const real sj = s0 * j0 + s1 * j1 + s2 * j2;
+  const real m = real(0.125) * rs * sj;
+  const real A = real(2) * w[0] + w[1] * s0 + w[2] * s1 + w[3] * s2 + w[4] * Hs;
+  const real c = real(0.125) * A;
+  const real crs = c * rs;
+  const real dH = m * w[4];
+  const real k = both ? real(2) : real(1);
+  lamWx[0] += k * (c * sj + dH * dHdr);
+  lamWx[1] += k * (crs * j0 + m * w[1] + dH * Wx[1]);
+  lamWx[2] += k * (crs * j1 + m * w[2] + dH * Wx[2]);
+  lamWx[3] += k * (crs * j2 + m * w[3] + dH * Wx[3]);
+  lamWx[4] += k * (real(0.5) * (w[1] * j0 + w[2] * j1 + w[3] * j2) + dH * dHdp);
+}
+
 // ---------------------------------------------------------------------------
 // kernels
 // ---------------------------------------------------------------------------
@@ -567,7 +595,7 @@ constexpr size_t adj_vol_smem(bool br2, bool split) {
   using C = Cfg<n>;
   return sizeof(real) * (C::NE * 15 * C::n3 + C::NE * 6 * 15 * C::n2 + C::n2 + 4 * n +
                          (br2 ? C::NE * C::n3 + C::NE * 6 * NV * C::n2 : 0) +
-                         (split ? C::n2 + C::NE * 14 * C::n3 : 0)) +
+                         (split ? C::n2 + C::NE * 15 * C::n3 : 0)) +
          sizeof(int) * C::NE * 8;
 }
 
@@ -594,8 +622,8 @@ __global__ void __launch_bounds__(Cfg<n>::T) k_adj_vol(
   real* sSJ = sOp + n2 + 4 * n;                 // BR2: [NE][n3] 1/J
   real* sBr = sSJ + (BR2 ? NE * n3 : 0);        // BR2: [NE][6][5][n2] adjoint of U* from the jumps
   real* sDT = sBr + (BR2 ? NE * 6 * NV * n2 : 0);  // SPLIT: DT[a * n + i] = D[i][a]
-  real* sWJ = sDT + (SPLIT ? n2 : 0);              // SPLIT: [NE][14][n3] W (5) and Ja (9) per node
-  int* sES = reinterpret_cast<int*>(sWJ + (SPLIT ? NE * 14 * n3 : 0));
+  real* sWJ = sDT + (SPLIT ? n2 : 0);              // SPLIT: [NE][15][n3] W (5), Ja (9) and H per node
+  int* sES = reinterpret_cast<int*>(sWJ + (SPLIT ? NE * 15 * n3 : 0));
   const int tid = threadIdx.x;
   const int el = tid / n3, node = tid - el * n3;
   const int e0 = blockIdx.x * NE;
@@ -628,11 +656,13 @@ __global__ void __launch_bounds__(Cfg<n>::T) k_adj_vol(
   for (int v = 0; v < NV; ++v) myb[v * n3 + node] = valid ? -lam[((size_t)e * NV + v) * n3 + node] * sj : real(0);
   if constexpr (SPLIT) {
     for (int t = tid; t < n2; t += T) sDT[t] = ops.DT[t];
-    real* wj = sWJ + el * 14 * n3 + node;
+    real* wj = sWJ + el * 15 * n3 + node;
 #pragma unroll
     for (int v = 0; v < NV; ++v) wj[v * n3] = W[v];
 #pragma unroll
     for (int c = 0; c < 9; ++c) wj[(NV + c) * n3] = jac[c];
+    // total enthalpy H = gamma/(gamma-1) p/rho + |u|^2/2 (the kinetic-energy-preserving pairs)
+    wj[14 * n3] = (ph.inv_gm1 + real(1)) * W[4] / W[0] + real(0.5) * (W[1] * W[1] + W[2] * W[2] + W[3] * W[3]);
   }
   // face-gradient adjoints of the element's six faces (own slot)
   __syncthreads();
@@ -679,7 +709,10 @@ __global__ void __launch_bounds__(Cfg<n>::T) k_adj_vol(
     // which it appears (weight D[a][i_x] lam_a), in one evaluation per partner
     const Phys<Dual<real>> pd = dual_phys(ph);
     const real* lv = myb;  // lam_vol [5][n3] of this element
-    const real* wj = sWJ + el * 14 * n3;
+    const real* wj = sWJ + el * 15 * n3;
+    // the node's own enthalpy and its partials with respect to rho and p (KEP pairs)
+    const real gg = ph.inv_gm1 + real(1), irx = real(1) / W[0];
+    const real Hx = wj[14 * n3 + node], dHdr = -gg * W[4] * irx * irx, dHdp = gg * irx;
 #pragma unroll 1
     for (int l = 0; l < 3; ++l) {
       const int ix = l == 0 ? i : (l == 1 ? j : k);
@@ -699,7 +732,10 @@ __global__ void __launch_bounds__(Cfg<n>::T) k_adj_vol(
           Wa[v] = wj[v * n3 + na];
           w[v] = a == ix ? dxa * lx[v] : dxa * lx[v] + dax * lv[v * n3 + na];
         }
-        split_pair_vjp<real, SPLIT>(W, Wa, Jx, Jpa, pd, w, a == ix, lamW);
+        if constexpr (SPLIT == 1)
+          kep_pair_vjp(W, Hx, dHdr, dHdp, Wa, wj[14 * n3 + na], Jx, Jpa, w, a == ix, lamW);
+        else
+          split_pair_vjp<real, SPLIT>(W, Wa, Jx, Jpa, pd, w, a == ix, lamW);
       }
       // strong-form face terms at the line ends: c Fcal^{c,l}(U_x)
       if (ix == 0 || ix == n - 1) {
