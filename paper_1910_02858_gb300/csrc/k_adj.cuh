@@ -370,58 +370,77 @@ __device__ void riemann_vjp_dual(const real WL[NV], const real WR[NV], const rea
   }
 }
 
-// 2 F#(W_x, W_a) in the direction of the pair's metric terms (Eq. semiDiscreteSplit):
-// SPLIT 1 Pirozzoli's kinetic-energy-preserving flux with Jx + Ja (the form the
-// forward kernel accumulates, D times this), SPLIT 2 twice Chandrashekar's
-// entropy-conservative flux with (Jx + Ja)/2.  T is the arithmetic or a dual number.
-template <typename T, int SPLIT>
-__device__ __forceinline__ void split_pair_flux(const T Wx[NV], const T Wa[NV], const T Jx[3], const T Ja[3],
-                                                const Phys<T>& ph, T F[NV]) {
-  if constexpr (SPLIT == 2) {
-    const T ux[3] = {Wx[1], Wx[2], Wx[3]}, ua[3] = {Wa[1], Wa[2], Wa[3]};
-    const T Jm[3] = {T(0.5) * (Jx[0] + Ja[0]), T(0.5) * (Jx[1] + Ja[1]), T(0.5) * (Jx[2] + Ja[2])};
-    ec_flux(Wx[0], ux, T(0.5) * Wx[0] / Wx[4], ux[0] * ux[0] + ux[1] * ux[1] + ux[2] * ux[2], Wa[0], ua,
-            T(0.5) * Wa[0] / Wa[4], ua[0] * ua[0] + ua[1] * ua[1] + ua[2] * ua[2], Jm, ph, F);
-#pragma unroll
-    for (int v = 0; v < NV; ++v) F[v] = T(2) * F[v];
+// Logarithmic mean L(a, b) = (a - b) / (ln a - ln b), its partial dL/da and 1/L, from
+// the variable f = (a - b)/(a + b), u = f^2 and F(u) = atanh(f)/f of Ismail and Roe:
+// L = (a + b) / (2F), dL/da = (1 - 4 f b F'(u) / (F (a + b))) / (2F), with the series of
+// F and F' = dF/du below u = 1e-2 (as in the forward log mean) and otherwise
+// F = ln(a/b) / (2f), F' = (1/(1-u) - F) / (2u).
+template <typename real>
+__device__ __forceinline__ void log_mean_d(real a, real b, real& L, real& dLda, real& iL) {
+  const real s = a + b;
+  const real is = real(1) / s;
+  const real f = (a - b) * is;
+  const real u = f * f;
+  real F, Fp;
+  if (u < real(1e-2)) {
+    F = real(1.0 / 15.0);
+    F = F * u + real(1.0 / 13.0);
+    F = F * u + real(1.0 / 11.0);
+    F = F * u + real(1.0 / 9.0);
+    F = F * u + real(1.0 / 7.0);
+    F = F * u + real(1.0 / 5.0);
+    F = F * u + real(1.0 / 3.0);
+    F = F * u + real(1);
+    Fp = real(7.0 / 15.0);
+    Fp = Fp * u + real(6.0 / 13.0);
+    Fp = Fp * u + real(5.0 / 11.0);
+    Fp = Fp * u + real(4.0 / 9.0);
+    Fp = Fp * u + real(3.0 / 7.0);
+    Fp = Fp * u + real(2.0 / 5.0);
+    Fp = Fp * u + real(1.0 / 3.0);
   } else {
-    const T Hx = (Wx[4] * ph.inv_gm1 + T(0.5) * Wx[0] * (Wx[1] * Wx[1] + Wx[2] * Wx[2] + Wx[3] * Wx[3]) + Wx[4]) / Wx[0];
-    const T Ha = (Wa[4] * ph.inv_gm1 + T(0.5) * Wa[0] * (Wa[1] * Wa[1] + Wa[2] * Wa[2] + Wa[3] * Wa[3]) + Wa[4]) / Wa[0];
-    const T rs = Wx[0] + Wa[0], us = Wx[1] + Wa[1], vs = Wx[2] + Wa[2], ws = Wx[3] + Wa[3];
-    const T ps = Wx[4] + Wa[4], Hs = Hx + Ha;
-    const T j0 = Jx[0] + Ja[0], j1 = Jx[1] + Ja[1], j2 = Jx[2] + Ja[2];
-    const T m = T(0.125) * rs * (us * j0 + vs * j1 + ws * j2);
-    const T hp = T(0.5) * ps;
-    F[0] = T(2) * m;
-    F[1] = m * us + hp * j0;
-    F[2] = m * vs + hp * j1;
-    F[3] = m * ws + hp * j2;
-    F[4] = m * Hs;
+    F = dg_log(a / b) / (real(2) * f);
+    Fp = (real(1) / (real(1) - u) - F) / (real(2) * u);
   }
+  const real iF = real(1) / F;
+  L = real(0.5) * s * iF;
+  iL = real(2) * F * is;
+  dLda = real(0.5) * iF * (real(1) - real(4) * f * b * Fp * iF * is);
 }
 
-// lamWx += d/dW_x (w . 2F#(W_x, W_a)); both = true: W_a is W_x (the diagonal pair)
-template <typename real, int SPLIT>
-__device__ __forceinline__ void split_pair_vjp(const real Wx[NV], const real Wa[NV], const real Jx[3],
-                                               const real Ja[3], const Phys<Dual<real>>& pd, const real w[NV],
-                                               bool both, real lamWx[NV]) {
-  using D = Dual<real>;
-  const D jx[3] = {D(Jx[0], real(0)), D(Jx[1], real(0)), D(Jx[2], real(0))};
-  const D ja[3] = {D(Ja[0], real(0)), D(Ja[1], real(0)), D(Ja[2], real(0))};
-#pragma unroll 1
-  for (int c = 0; c < NV; ++c) {
-    D x[NV], a[NV], F[NV];
+// Chandrashekar's pair flux reversed by hand: lamWx += d/dW_x (w . 2F#(W_x, W_a)), F# the
+// entropy-conservative two-point flux in the averaged direction Jm = (Jx + Ja)/2.  With
+// um = (u_x + u_a)/2, Un = um . Jm, f_rho = L(rho) Un, p~ = (rho_x + rho_a) / (2 (beta_x + beta_a)),
+// E' = 1/(2 (gamma-1) L(beta)) - (|u_x|^2 + |u_a|^2)/4:  w . F# = f_rho B + p~ C with
+// B = w_0 + w_1..3 . um + w_4 (E' + |um|^2) and C = w_1..3 . Jm + w_4 Un, whose partials reach W_x
+// through L(rho), um, |u_x|^2, p~ and beta_x = rho_x / (2 p_x) (given per node with 1/p_x).
+// both: W_a is W_x (the diagonal pair), twice the one-sided gradient.
+template <typename real>
+__device__ __forceinline__ void ec_pair_vjp(const real Wx[NV], real bx, real ipx, real qx, const real Wa[NV],
+                                            real ba, const real Jx[3], const real Ja[3], real inv_gm1,
+                                            const real w[NV], bool both, real lamWx[NV]) {
+  const real Jm[3] = {real(0.5) * (Jx[0] + Ja[0]), real(0.5) * (Jx[1] + Ja[1]), real(0.5) * (Jx[2] + Ja[2])};
+  const real um[3] = {real(0.5) * (Wx[1] + Wa[1]), real(0.5) * (Wx[2] + Wa[2]), real(0.5) * (Wx[3] + Wa[3])};
+  const real Un = um[0] * Jm[0] + um[1] * Jm[1] + um[2] * Jm[2];
+  real Lr, dLr, iLr, Lb, dLb, iLb;
+  log_mean_d(Wx[0], Wa[0], Lr, dLr, iLr);
+  log_mean_d(bx, ba, Lb, dLb, iLb);
+  const real qa = Wa[1] * Wa[1] + Wa[2] * Wa[2] + Wa[3] * Wa[3];
+  const real frho = Lr * Un;
+  const real ibs = real(1) / (bx + ba);
+  const real pt = real(0.5) * (Wx[0] + Wa[0]) * ibs;
+  const real Ep = real(0.5) * inv_gm1 * iLb - real(0.25) * (qx + qa);
+  const real B = w[0] + w[1] * um[0] + w[2] * um[1] + w[3] * um[2] +
+                 w[4] * (Ep + um[0] * um[0] + um[1] * um[1] + um[2] * um[2]);
+  const real C = w[1] * Jm[0] + w[2] * Jm[1] + w[3] * Jm[2] + w[4] * Un;
+  const real d_bx = -real(0.5) * inv_gm1 * frho * w[4] * iLb * iLb * dLb - C * pt * ibs;
+  const real k = both ? real(4) : real(2);  // 2 F#, and twice that for the diagonal pair
+  const real cu = B * Lr, c4 = pt * w[4], fw = frho * w[4];
+  lamWx[0] += k * (B * Un * dLr + real(0.5) * C * ibs + real(0.5) * d_bx * ipx);
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      x[v] = D(Wx[v], v == c ? real(1) : real(0));
-      a[v] = D(Wa[v], (both && v == c) ? real(1) : real(0));
-    }
-    split_pair_flux<D, SPLIT>(x, a, jx, ja, pd, F);
-    real sdot = real(0);
-#pragma unroll
-    for (int v = 0; v < NV; ++v) sdot += w[v] * F[v].d;
-    lamWx[c] += sdot;
-  }
+  for (int c = 0; c < 3; ++c)
+    lamWx[1 + c] += k * real(0.5) * ((cu + c4) * Jm[c] + frho * w[1 + c] + fw * (real(2) * um[c] - Wx[1 + c]));
+  lamWx[4] -= k * d_bx * bx * ipx;
 }
 
 // Pirozzoli's pair flux reversed by hand: lamWx += d/dW_x (w . 2F#(W_x, W_a)).  With the
@@ -604,7 +623,7 @@ constexpr size_t adj_vol_smem(bool br2, bool split) {
 // Jm_f = (U* - W_own) n s_hat; their adjoints reach U* (added to LWs) and the
 // element's own face state (added to its slot of LWf, written by k_adj_face).
 // SPLIT (Gauss-Lobatto): the reverse of the split-form volume integral: the viscous
-// part as in the standard form, the two-point advective sums by dual numbers per
+// part as in the standard form, the two-point advective sums reversed by hand per
 // pair (each node collects d/dW of both ordered pairs it takes part in) and the
 // strong-form face terms at the line ends.
 template <typename real, int n, bool BR2, int SPLIT>
@@ -661,8 +680,10 @@ __global__ void __launch_bounds__(Cfg<n>::T) k_adj_vol(
     for (int v = 0; v < NV; ++v) wj[v * n3] = W[v];
 #pragma unroll
     for (int c = 0; c < 9; ++c) wj[(NV + c) * n3] = jac[c];
-    // total enthalpy H = gamma/(gamma-1) p/rho + |u|^2/2 (the kinetic-energy-preserving pairs)
-    wj[14 * n3] = (ph.inv_gm1 + real(1)) * W[4] / W[0] + real(0.5) * (W[1] * W[1] + W[2] * W[2] + W[3] * W[3]);
+    // kinetic-energy-preserving pairs: total enthalpy H = gamma/(gamma-1) p/rho + |u|^2/2;
+    // entropy-conservative pairs: beta = rho / (2 p)
+    wj[14 * n3] = SPLIT == 1 ? (ph.inv_gm1 + real(1)) * W[4] / W[0] + real(0.5) * (W[1] * W[1] + W[2] * W[2] + W[3] * W[3])
+                             : real(0.5) * W[0] / W[4];
   }
   // face-gradient adjoints of the element's six faces (own slot)
   __syncthreads();
@@ -707,12 +728,14 @@ __global__ void __launch_bounds__(Cfg<n>::T) k_adj_vol(
     // advective part: sum_l sum_a D_{i_l a} 2F#(x, a) at every node x; node x collects
     // d/dW_x of its own sums (weight D[i_x][a] lam_x) and of its partners' sums in
     // which it appears (weight D[a][i_x] lam_a), in one evaluation per partner
-    const Phys<Dual<real>> pd = dual_phys(ph);
     const real* lv = myb;  // lam_vol [5][n3] of this element
     const real* wj = sWJ + el * 15 * n3;
-    // the node's own enthalpy and its partials with respect to rho and p (KEP pairs)
-    const real gg = ph.inv_gm1 + real(1), irx = real(1) / W[0];
-    const real Hx = wj[14 * n3 + node], dHdr = -gg * W[4] * irx * irx, dHdp = gg * irx;
+    // per node: the enthalpy and its partials with respect to rho and p (KEP pairs), or
+    // beta, 1/p and |u|^2 (EC pairs)
+    const real gg = ph.inv_gm1 + real(1), irx = real(1) / W[0], ipx = real(1) / W[4];
+    const real x14 = wj[14 * n3 + node];  // this node's staged H (KEP) or beta (EC)
+    const real dHdr = -gg * W[4] * irx * irx, dHdp = gg * irx;
+    const real qx = W[1] * W[1] + W[2] * W[2] + W[3] * W[3];
 #pragma unroll 1
     for (int l = 0; l < 3; ++l) {
       const int ix = l == 0 ? i : (l == 1 ? j : k);
@@ -733,9 +756,9 @@ __global__ void __launch_bounds__(Cfg<n>::T) k_adj_vol(
           w[v] = a == ix ? dxa * lx[v] : dxa * lx[v] + dax * lv[v * n3 + na];
         }
         if constexpr (SPLIT == 1)
-          kep_pair_vjp(W, Hx, dHdr, dHdp, Wa, wj[14 * n3 + na], Jx, Jpa, w, a == ix, lamW);
+          kep_pair_vjp(W, x14, dHdr, dHdp, Wa, wj[14 * n3 + na], Jx, Jpa, w, a == ix, lamW);
         else
-          split_pair_vjp<real, SPLIT>(W, Wa, Jx, Jpa, pd, w, a == ix, lamW);
+          ec_pair_vjp(W, x14, ipx, qx, Wa, wj[14 * n3 + na], Jx, Jpa, ph.inv_gm1, w, a == ix, lamW);
       }
       // strong-form face terms at the line ends: c Fcal^{c,l}(U_x)
       if (ix == 0 || ix == n - 1) {
