@@ -172,12 +172,12 @@ template <typename real, int n, bool LGL>
 __device__ __forceinline__ void faces_from_volume(const real* __restrict__ sU, const Ops<real>& ops,
                                                   const int* __restrict__ sES, int e0, int K, int S,
                                                   real* __restrict__ Wf, const Phys<real>& ph,
-                                                  unsigned* __restrict__ status, int tid) {
+                                                  unsigned* __restrict__ status, int tid, int T = Cfg<n>::T) {
   using C = Cfg<n>;
   constexpr int n2 = C::n2, n3p = C::n3p, P = C::P;
   if constexpr (sizeof(real) == 8) {
     // FP64 (FP64-pipe bound): one thread per face node keeps more warps on the pipe
-    for (int it = tid; it < C::NE * 6 * n2; it += C::T) {
+    for (int it = tid; it < C::NE * 6 * n2; it += T) {
       const int el = it / (6 * n2);
       const int r = it - el * 6 * n2;
       const int s = r / n2, pq = r - s * n2;
@@ -251,7 +251,7 @@ __device__ __forceinline__ void faces_from_volume(const real* __restrict__ sU, c
       for (int v = 0; v < NV; ++v) dst[v * n2] = W[v];
     }
   };
-  for (int it = tid; it < C::NE * 3 * n2; it += C::T) {
+  for (int it = tid; it < C::NE * 3 * n2; it += T) {
     const int el = it / (3 * n2);
     const int r = it - el * 3 * n2;
     const int l = r / n2, line = r - l * n2;
@@ -330,6 +330,57 @@ __global__ void k_bc(const double* __restrict__ xbc, const int* __restrict__ bcK
 // ---------------------------------------------------------------------------
 // a2-a4, a6, a7: lifting, gradient prolongation, volume integral
 // ---------------------------------------------------------------------------
+// BR1 surface terms of the lifting for the NE elements of a CTA: Q = U* n_d s_hat with
+// the element's outward normal at every face node ([NE][6][15][n^2], component v*3+d;
+// big sides of mortars: the projected lifting flux of their small sides), the
+// master-frame node of each face node (sMpq, reused by the gradient prolongation) and,
+// with BR2, the jumps (U* - U_e) n s_hat with the element's own face state.
+// T threads from tid; no barrier.
+template <typename real, int n, int NE, bool BR2>
+__device__ __forceinline__ void br1_surface_terms(const real* __restrict__ Wf, const real* __restrict__ fgeo,
+                                                  const real* __restrict__ QB, const int* __restrict__ sES,
+                                                  real* __restrict__ sQ, int* __restrict__ sMpq,
+                                                  real* __restrict__ sJm, int e0, int K, int S, int bigBase, int tid,
+                                                  int T) {
+  constexpr int n2 = n * n;
+  for (int it = tid; it < NE * 6 * n2; it += T) {
+    const int el2 = it / (6 * n2);
+    const int r = it - el2 * 6 * n2;
+    const int s = r / n2, pq = r - s * n2;
+    if (e0 + el2 >= K) continue;
+    const int es = sES[el2 * 6 + s];
+    const int side = es_side(es);
+    const int mpq = orient_pq(es_orient(es), n - 1, pq % n, pq / n);
+    sMpq[it] = mpq;  // reused by the gradient prolongation
+    const real* w0 = Wf + ((size_t)side * NV) * n2 + mpq;
+    const real* w1 = Wf + ((size_t)(S + side) * NV) * n2 + mpq;
+    const real* g = fgeo + ((size_t)side * 4) * n2 + mpq;
+    const real sc = es_slave(es) ? -g[3 * n2] : g[3 * n2];
+    const real nd[3] = {g[0] * sc, g[n2] * sc, g[2 * n2] * sc};
+    real* Q = sQ + ((el2 * 6 + s) * 15) * n2 + pq;
+    if (side >= bigBase) {
+      const real* qb = QB + ((size_t)(side - bigBase) * 15) * n2 + mpq;
+#pragma unroll
+      for (int c = 0; c < 15; ++c) Q[c * n2] = qb[c * n2];
+    } else {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const real ws = real(0.5) * (w0[v * n2] + w1[v * n2]);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) Q[(v * 3 + d) * n2] = ws * nd[d];
+      }
+    }
+    if constexpr (BR2) {  // jump (U* - U_e) n s_hat with the element's own face state
+      const real* wo = es_slave(es) ? w1 : w0;
+      real* Jm = sJm + ((el2 * 6 + s) * 15) * n2 + pq;
+#pragma unroll
+      for (int v = 0; v < NV; ++v)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) Jm[(v * 3 + d) * n2] = Q[(v * 3 + d) * n2] - wo[v * n2] * nd[d];
+    }
+  }
+}
+
 // Resident CTAs per SM asked of the register allocator, from measurements: FP32
 // CUDA-core form two of 512 threads at n = 8 and five of 216 at n = 6 (standard
 // form); FP64 an explicit minimum of one, which lets the compiler take more
@@ -408,44 +459,7 @@ __device__ __forceinline__ void lift_vol_body(
   BFrag<SW> bfr;
   if constexpr (SW != 0) bfr = make_bfrag<n, SW>(reinterpret_cast<const float*>(sOp), tid & 31);
 
-  // BR1 surface terms: Q = U* n_d s_hat with the element's outward normal (big
-  // sides of mortars: the projected lifting flux of their small sides)
-  for (int it = tid; it < NE * 6 * n2; it += T) {
-    const int el2 = it / (6 * n2);
-    const int r = it - el2 * 6 * n2;
-    const int s = r / n2, pq = r - s * n2;
-    if (e0 + el2 >= K) continue;
-    const int es = sES[el2 * 6 + s];
-    const int side = es_side(es);
-    const int mpq = orient_pq(es_orient(es), n - 1, pq % n, pq / n);
-    sMpq[it] = mpq;  // reused by the gradient prolongation
-    const real* w0 = Wf + ((size_t)side * NV) * n2 + mpq;
-    const real* w1 = Wf + ((size_t)(S + side) * NV) * n2 + mpq;
-    const real* g = fgeo + ((size_t)side * 4) * n2 + mpq;
-    const real sc = es_slave(es) ? -g[3 * n2] : g[3 * n2];
-    const real nd[3] = {g[0] * sc, g[n2] * sc, g[2 * n2] * sc};
-    real* Q = sQ + ((el2 * 6 + s) * 15) * n2 + pq;
-    if (side >= bigBase) {
-      const real* qb = QB + ((size_t)(side - bigBase) * 15) * n2 + mpq;
-#pragma unroll
-      for (int c = 0; c < 15; ++c) Q[c * n2] = qb[c * n2];
-    } else {
-#pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        const real ws = real(0.5) * (w0[v * n2] + w1[v * n2]);
-#pragma unroll
-        for (int d = 0; d < 3; ++d) Q[(v * 3 + d) * n2] = ws * nd[d];
-      }
-    }
-    if constexpr (BR2) {  // jump (U* - U_e) n s_hat with the element's own face state
-      const real* wo = es_slave(es) ? w1 : w0;
-      real* Jm = sJm + ((el2 * 6 + s) * 15) * n2 + pq;
-#pragma unroll
-      for (int v = 0; v < NV; ++v)
-#pragma unroll
-        for (int d = 0; d < 3; ++d) Jm[(v * 3 + d) * n2] = Q[(v * 3 + d) * n2] - wo[v * n2] * nd[d];
-    }
-  }
+  br1_surface_terms<real, n, NE, BR2>(Wf, fgeo, QB, sES, sQ, sMpq, sJm, e0, K, S, bigBase, tid, T);
 
   real G[15];
   real* myb = sbuf + el * 15 * n3p;
@@ -897,6 +911,151 @@ __global__ void __launch_bounds__(Cfg<n>::T, lift_vol_min_blocks<real, n, SW, SP
 #undef FLEXI_LIFT_VOL_PARAMS
 #undef FLEXI_LIFT_VOL_ARGS
 
+// a2-a4, a6, a7 for small FP64 meshes (fewer elements than SMs, n <= 4; standard form,
+// BR1): one element per CTA, spread over three thread groups of n^3 threads.  The lifting
+// computes one gradient component per group, the physical fluxes one direction per group,
+// the contravariant fluxes and the D_hat volume sweep one reference direction per group
+// (their partial sums added at the end), with the fields exchanged through shared memory.
+// The arithmetic is that of k_lift_vol; the three groups give the SMs that such meshes
+// occupy three times the warps to hide the FP64 pipe's latency.
+template <int n, bool LGL>
+__global__ void __launch_bounds__(3 * n * n * n) k_lift_vol_g3(
+    const double* __restrict__ U, const double* __restrict__ Ja, const double* __restrict__ sJ,
+    const double* __restrict__ Wf, const double* __restrict__ fgeo, const int* __restrict__ elemSide,
+    double* __restrict__ Gf, double* __restrict__ Utv, double* __restrict__ Gvol, int K, int S, int bigBase,
+    const double* __restrict__ QB, Ops<double> ops, Phys<double> ph) {
+  using real = double;
+  constexpr int n2 = n * n, n3 = n2 * n, T = 3 * n3, n3p = Cfg<n>::n3p;
+  __shared__ real sbuf[3 * 15 * n3p];  // three regions of 15 padded fields
+  __shared__ real sQ[6 * 15 * n2];     // BR1 surface terms [6][15][n2]
+  __shared__ real sOp[n2 + 4 * n];
+  __shared__ int sES[6], sSlot[6], sMpq[6 * n2];
+  const int tid = threadIdx.x;
+  const int g = tid / n3, node = tid - g * n3;
+  const int e = blockIdx.x;  // grid = K
+  const int i = node % n, j = (node / n) % n, k = node / n2;
+  const int pn = pidx<n>(i, j, k);
+  load_ops<real, n>(sOp, ops, tid, T);
+  if (tid < 6) {
+    const int es = elemSide[(size_t)e * 6 + tid];
+    sES[tid] = es;
+    sSlot[tid] = es_slave(es) * S + es_side(es);
+  }
+  real Uo[NV], W[NV], jac[9];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) Uo[v] = U[((size_t)e * NV + v) * n3 + node];
+#pragma unroll
+  for (int c = 0; c < 9; ++c) jac[c] = Ja[((size_t)e * 9 + c) * n3 + node];
+  const real sj = sJ[(size_t)e * n3 + node];
+  cons_to_prim(Uo, W, ph);
+  __syncthreads();
+  br1_surface_terms<real, n, 1, false>(Wf, fgeo, QB, sES, sQ, sMpq, nullptr, e, K, S, bigBase, tid, T);
+
+  // the group's column (Ja^l_g, l = 0..2) and row (Ja^g_d, d = 0..2) of the metric terms,
+  // selected by value (a runtime index would put jac in local memory)
+  auto pick = [g](real a, real b, real c) { return g == 0 ? a : (g == 1 ? b : c); };
+  const real col[3] = {pick(jac[0], jac[1], jac[2]), pick(jac[3], jac[4], jac[5]), pick(jac[6], jac[7], jac[8])};
+  const real row[3] = {pick(jac[0], jac[3], jac[6]), pick(jac[1], jac[4], jac[7]), pick(jac[2], jac[5], jac[8])};
+  // lifting, gradient component d = g: Ja^l_g W_v staged as field l*5 + v of region g
+  real* myb = sbuf + g * 15 * n3p;
+#pragma unroll
+  for (int l = 0; l < 3; ++l)
+#pragma unroll
+    for (int v = 0; v < NV; ++v) myb[(l * NV + v) * n3p + pn] = col[l] * W[v];
+  __syncthreads();
+  real acc[NV] = {real(0), real(0), real(0), real(0), real(0)};
+  node_sweep3<real, n>(sOp, myb, i, j, k, acc);
+  const real* lhm = sOp + n2 + 2 * n;
+  const real* lhp = sOp + n2 + 3 * n;
+  const int pq0 = j + n * k, pq1 = i + n * k, pq2 = i + n * j;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const int o = (v * 3 + g) * n2;
+    real a = acc[v];
+    if constexpr (LGL) {  // only nodes on a face receive its term
+      if (i == 0) a = dg_fma(lhm[0], sQ[0 * 15 * n2 + o + pq0], a);
+      if (i == n - 1) a = dg_fma(lhp[n - 1], sQ[1 * 15 * n2 + o + pq0], a);
+      if (j == 0) a = dg_fma(lhm[0], sQ[2 * 15 * n2 + o + pq1], a);
+      if (j == n - 1) a = dg_fma(lhp[n - 1], sQ[3 * 15 * n2 + o + pq1], a);
+      if (k == 0) a = dg_fma(lhm[0], sQ[4 * 15 * n2 + o + pq2], a);
+      if (k == n - 1) a = dg_fma(lhp[n - 1], sQ[5 * 15 * n2 + o + pq2], a);
+    } else {
+      a = dg_fma(lhm[i], sQ[0 * 15 * n2 + o + pq0], a);
+      a = dg_fma(lhp[i], sQ[1 * 15 * n2 + o + pq0], a);
+      a = dg_fma(lhm[j], sQ[2 * 15 * n2 + o + pq1], a);
+      a = dg_fma(lhp[j], sQ[3 * 15 * n2 + o + pq1], a);
+      a = dg_fma(lhm[k], sQ[4 * 15 * n2 + o + pq2], a);
+      a = dg_fma(lhp[k], sQ[5 * 15 * n2 + o + pq2], a);
+    }
+    acc[v] = a;
+  }
+  __syncthreads();  // every region read: region 0 takes the gradients
+  real* sG = sbuf;  // [15][n3p], component d*5 + v
+#pragma unroll
+  for (int v = 0; v < NV; ++v) sG[(g * NV + v) * n3p + pn] = acc[v] * sj;
+  __syncthreads();
+  real G[15];
+#pragma unroll
+  for (int c = 0; c < 15; ++c) G[c] = sG[c * n3p + pn];
+  if (Gvol != nullptr && g == 0) {
+#pragma unroll
+    for (int c = 0; c < 15; ++c) Gvol[((size_t)e * 15 + c) * n3 + node] = G[c];
+  }
+  // a4: gradients to the faces, one thread per (face node, component)
+  for (int it = tid; it < 6 * 15 * n2; it += T) {
+    const int s = it / (15 * n2);
+    const int r = it - s * 15 * n2;
+    const int c = r / n2, pq = r - c * n2;
+    const int l = s >> 1, p = pq % n, q = pq / n;
+    const real* b = sG + c * n3p;
+    real val = real(0);
+    if (LGL) {
+      val = b[pvol_index<n>(l, (s & 1) ? n - 1 : 0, p, q)];
+    } else {
+#pragma unroll
+      for (int a = 0; a < n; ++a) val = dg_fma((s & 1) ? ops.lp[a] : ops.lm[a], b[pvol_index<n>(l, a, p, q)], val);
+    }
+    Gf[((size_t)sSlot[s] * 15 + c) * n2 + sMpq[s * n2 + pq]] = val;
+  }
+  // a6: physical flux of direction d = g into region 1, then the contravariant flux of
+  // reference direction l = g (sum_d Ja^g_d F_d) into region 2
+  real F[NV];
+  if (g == 0)  // compile-time directions (flux_total indexes its arrays with d)
+    flux_total(Uo, W, G, 0, ph, F);
+  else if (g == 1)
+    flux_total(Uo, W, G, 1, ph, F);
+  else
+    flux_total(Uo, W, G, 2, ph, F);
+  real* sF = sbuf + 15 * n3p;
+  real* sC = sbuf + 2 * 15 * n3p;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) sF[(g * NV + v) * n3p + pn] = F[v];
+  __syncthreads();
+#pragma unroll
+  for (int v = 0; v < NV; ++v)
+    sC[(g * NV + v) * n3p + pn] = dg_fma(row[2], sF[(2 * NV + v) * n3p + pn],
+                                         dg_fma(row[1], sF[(NV + v) * n3p + pn], row[0] * sF[v * n3p + pn]));
+  __syncthreads();
+  // a7: D_hat sweep along direction l = g; the partial sums go to region 1 (no longer read)
+  const int il = g == 0 ? i : (g == 1 ? j : k);
+  real sum[NV] = {real(0), real(0), real(0), real(0), real(0)};
+#pragma unroll
+  for (int a = 0; a < n; ++a) {
+    const real dh = sOp[a * n + il];
+    const int ia = g == 0 ? pidx<n>(a, j, k) : (g == 1 ? pidx<n>(i, a, k) : pidx<n>(i, j, a));
+#pragma unroll
+    for (int v = 0; v < NV; ++v) sum[v] = dg_fma(dh, sC[(g * NV + v) * n3p + ia], sum[v]);
+  }
+#pragma unroll
+  for (int v = 0; v < NV; ++v) sF[(g * NV + v) * n3p + pn] = sum[v];
+  __syncthreads();
+  if (g == 0) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+      Utv[((size_t)e * NV + v) * n3 + node] = sF[v * n3p + pn] + sF[(NV + v) * n3p + pn] + sF[(2 * NV + v) * n3p + pn];
+  }
+}
+
 template <typename real, int n, int SW, bool LGL, int SPLIT, bool BR2>
 constexpr auto lift_vol_kernel() {
   if constexpr (lift_vol_min_blocks<real, n, SW, SPLIT, BR2>() > 0)
@@ -956,26 +1115,82 @@ __global__ void __launch_bounds__(128, sizeof(real) == 4 ? 8 : 1) k_face(const r
   for (int v = 0; v < NV; ++v) Ff[((size_t)side * NV + v) * n2 + pq] = (f[v] - real(0.5) * (fl[v] + fr[v])) * sa;
 }
 
+// The same flux for small meshes (few face nodes per SM): 32 face nodes per CTA of three
+// warps, warp 0 computing the Riemann flux, warps 1 and 2 the viscous normal fluxes of
+// the two sides, combined through shared memory.  Each thread runs a third of the
+// dependent FP64 chain of k_face, which is what bounds a mesh that leaves most SMs idle.
+template <typename real, int n, int RS>
+__global__ void __launch_bounds__(96) k_face3(const real* __restrict__ Wf, const real* __restrict__ Gf,
+                                              const real* __restrict__ fgeo, real* __restrict__ Ff, int S,
+                                              int nSface, int nBC, Phys<real> ph) {
+  constexpr int n2 = n * n;
+  __shared__ real sf[3][NV][32];
+  const int role = threadIdx.x >> 5, lane = threadIdx.x & 31;  // warp-uniform role
+  const int idx = blockIdx.x * 32 + lane;
+  const bool live = idx < nSface * n2;
+  const int side = live ? idx / n2 : 0, pq = live ? idx - side * n2 : 0;
+  real nv[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) nv[d] = fgeo[((size_t)side * 4 + d) * n2 + pq];
+  const bool bnd = side < nBC;
+  real out[NV];
+  if (role == 0) {
+    real WL[NV], WR[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      WL[v] = Wf[((size_t)side * NV + v) * n2 + pq];
+      WR[v] = Wf[((size_t)(S + side) * NV + v) * n2 + pq];
+    }
+    riemann_kind<RS>(WL, WR, real(1) / WL[0], real(1) / WR[0], nv, ph, out);
+  } else {
+    // role 1: the master (slot 0) side, role 2: the slave or boundary (slot 1) side,
+    // whose gradients on a boundary are the inner ones
+    const int slot = role - 1;
+    real Wx[NV], Gx[15];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Wx[v] = Wf[((size_t)(slot * S + side) * NV + v) * n2 + pq];
+    const int gslot = bnd ? 0 : slot;
+#pragma unroll
+    for (int c = 0; c < 15; ++c) Gx[c] = Gf[((size_t)(gslot * S + side) * 15 + c) * n2 + pq];
+    visc_normal(Wx, real(1) / Wx[0], Gx, nv, ph, out);
+  }
+#pragma unroll
+  for (int v = 0; v < NV; ++v) sf[role][v][lane] = out[v];
+  __syncthreads();
+  if (role == 0 && live) {
+    const real sa = fgeo[((size_t)side * 4 + 3) * n2 + pq];
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+      Ff[((size_t)side * NV + v) * n2 + pq] = (sf[0][v][lane] - real(0.5) * (sf[1][v][lane] + sf[2][v][lane])) * sa;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // a8-a10: surface integral, -1/J, RK stage update, face states of the new U
 // ---------------------------------------------------------------------------
-template <typename real, int n, int MODE, bool LGL>
-__global__ void __launch_bounds__(Cfg<n>::T, (sizeof(real) == 4 && Cfg<n>::T == 512) ? 4 : ((sizeof(real) == 4 && Cfg<n>::T == 216) ? 8 : 2)) k_surf(
+// TM > 1 (small meshes): TM times the threads, the first NE n^3 of them one per node, all
+// of them sharing the loops over face nodes (the gather of the face fluxes and the face
+// states of the new U), which otherwise take several dependent rounds of global-memory
+// latency per thread on a mesh that leaves most SMs idle.
+template <typename real, int n, int MODE, bool LGL, int TM = 1>
+__global__ void __launch_bounds__(Cfg<n>::T * TM, TM > 1 ? 1 : ((sizeof(real) == 4 && Cfg<n>::T == 512) ? 4 : ((sizeof(real) == 4 && Cfg<n>::T == 216) ? 8 : 2))) k_surf(
     const real* __restrict__ Ff, const int* __restrict__ elemSide, const real* __restrict__ sJ,
     const real* __restrict__ Utv, real* __restrict__ U, real* __restrict__ dU, real* __restrict__ Ut,
     real* __restrict__ Wf, const double* __restrict__ xsol, RkStage<real> rk, double t, SourceParams src, int K,
     int S, Ops<real> ops, Phys<real> ph, unsigned* __restrict__ status) {
   using C = Cfg<n>;
-  constexpr int n2 = C::n2, n3 = C::n3, NE = C::NE, T = C::T;
+  constexpr int n2 = C::n2, n3 = C::n3, NE = C::NE, T = C::T * TM;
   __shared__ real sF[NE * 6 * NV * n2];
   __shared__ real sU[(MODE == 1) ? NE * NV * C::n3p : 1];
   __shared__ real sOp[n2 + 4 * n];
   __shared__ int sES[NE * 6];
   const int tid = threadIdx.x;
-  const int el = tid / n3, node = tid - el * n3;
+  const bool nodeThread = TM == 1 || tid < C::T;
+  const int tn = nodeThread ? tid : 0;
+  const int el = tn / n3, node = tn - el * n3;
   const int e0 = blockIdx.x * NE;
   const int e = e0 + el;
-  const bool valid = e < K;
+  const bool valid = nodeThread && e < K;
   const int i = node % n, j = (node / n) % n, k = node / n2;
   // the node's own global values are requested first, so that their latency
   // overlaps the gather of the face fluxes and the barrier
@@ -1072,13 +1287,13 @@ __global__ void __launch_bounds__(Cfg<n>::T, (sizeof(real) == 4 && Cfg<n>::T == 
         U[g] = un;
         sU[(el * NV + v) * C::n3p + pidx<n>(i, j, k)] = un;
       }
-    } else {
+    } else if (nodeThread) {
 #pragma unroll
       for (int v = 0; v < NV; ++v) sU[(el * NV + v) * C::n3p + pidx<n>(i, j, k)] = (v == 0 || v == 4) ? real(1) : real(0);
     }
     if (rk.prolong) {
       __syncthreads();
-      faces_from_volume<real, n, LGL>(sU, ops, sES, e0, K, S, Wf, ph, status, tid);
+      faces_from_volume<real, n, LGL>(sU, ops, sES, e0, K, S, Wf, ph, status, tid, T);
     }
   }
 }
@@ -1155,6 +1370,27 @@ cudaError_t launch_lift_vol(const DevMesh& m, const real* U, const Ops<real>& op
       FLEXI_DISPATCH_N(m.n, return lift_vol_n<real, NN, 2>(m, U, ops, ph, store_grad, st));
     }
   }
+  if constexpr (sizeof(real) == 8) {
+    // fewer elements than SMs at n <= 4: three thread groups per element (k_lift_vol_g3)
+    if (!m.br2 && m.split == 0 && m.n <= 4 && m.K < m.nsm) {
+#define FLEXI_G3(NN, LG)                                                                                   \
+  k_lift_vol_g3<NN, LG><<<m.K, 3 * NN * NN * NN, 0, st>>>(                                                 \
+      U, (const double*)m.Ja, (const double*)m.sJ, (const double*)m.Wf, (const double*)m.fgeo, m.elemSide, \
+      (double*)m.Gf, (double*)m.Utv, store_grad ? (double*)m.Gvol : nullptr, m.K, m.S, m.Sface,           \
+      (const double*)m.QB, ops, ph)
+      switch (m.n * 2 + m.lgl) {
+        case 4: FLEXI_G3(2, false); break;
+        case 5: FLEXI_G3(2, true); break;
+        case 6: FLEXI_G3(3, false); break;
+        case 7: FLEXI_G3(3, true); break;
+        case 8: FLEXI_G3(4, false); break;
+        case 9: FLEXI_G3(4, true); break;
+        default: return cudaErrorInvalidValue;
+      }
+#undef FLEXI_G3
+      return cudaGetLastError();
+    }
+  }
   if (m.br2) {
     if (m.lgl) {
       FLEXI_DISPATCH_N(m.n, return lift_vol_n<real, NN, 0, true, 0, true>(m, U, ops, ph, store_grad, st));
@@ -1178,9 +1414,23 @@ template <typename real>
 cudaError_t launch_face(const DevMesh& m, const Phys<real>& ph, cudaStream_t st) {
   const int tot = m.Sface * m.n * m.n;  // big sides of mortars get their flux by projection
   if (tot == 0) return cudaSuccess;
-  // one warp per CTA when 128-thread CTAs would leave SMs idle (small meshes: the
-  // FP64 flux is pipe-bound per SM, so spreading the face nodes over more SMs pays)
-  const int TB = (tot + 127) / 128 >= 2 * m.nsm ? 128 : 32;
+  // small meshes (128-thread CTAs would leave SMs idle): three warps per 32 face nodes
+  if ((tot + 127) / 128 < 2 * m.nsm) {
+    const int grid = (tot + 31) / 32;
+#define FLEXI_FACE3(RSV)                                                                                    \
+  FLEXI_DISPATCH_N(m.n, (k_face3<real, NN, RSV><<<grid, 96, 0, st>>>((const real*)m.Wf, (const real*)m.Gf, \
+                                                                    (const real*)m.fgeo, (real*)m.Ff, m.S, \
+                                                                    m.Sface, m.nBC, ph)))
+    switch (ph.riemann) {
+      case 1: FLEXI_FACE3(1); break;
+      case 3: FLEXI_FACE3(3); break;
+      case 4: FLEXI_FACE3(4); break;
+      default: FLEXI_FACE3(0); break;
+    }
+#undef FLEXI_FACE3
+    return cudaGetLastError();
+  }
+  const int TB = 128;
   switch (ph.riemann) {
     case 1:
       FLEXI_DISPATCH_N(m.n, (k_face<real, NN, 1><<<(tot + TB - 1) / TB, TB, 0, st>>>(
@@ -1207,14 +1457,24 @@ static cudaError_t surf_n(const DevMesh& m, int mode, real* U, real* dU, real* U
                           const SourceParams& src, const Ops<real>& ops, const Phys<real>& ph, cudaStream_t st) {
   using C = Cfg<n>;
   const int grid = (m.K + C::NE - 1) / C::NE;
+#define FLEXI_SURF(MODEV, TMV)                                                                                    \
+  k_surf<real, n, MODEV, LGL, TMV><<<grid, C::T * TMV, 0, st>>>((const real*)m.Ff, m.elemSide, (const real*)m.sJ, \
+                                                                 (const real*)m.Utv, U, dU, Ut, (real*)m.Wf, m.xsol, \
+                                                                 rk, t, src, m.K, m.S, ops, ph, m.status)
+  if constexpr (n <= 4) {
+    if (grid < m.nsm) {  // fewer CTAs than SMs: six times the threads for the face loops
+      if (mode == 0)
+        FLEXI_SURF(0, 6);
+      else
+        FLEXI_SURF(1, 6);
+      return cudaGetLastError();
+    }
+  }
   if (mode == 0)
-    k_surf<real, n, 0, LGL><<<grid, C::T, 0, st>>>((const real*)m.Ff, m.elemSide, (const real*)m.sJ,
-                                                   (const real*)m.Utv, U, dU, Ut, (real*)m.Wf, m.xsol, rk, t, src,
-                                                   m.K, m.S, ops, ph, m.status);
+    FLEXI_SURF(0, 1);
   else
-    k_surf<real, n, 1, LGL><<<grid, C::T, 0, st>>>((const real*)m.Ff, m.elemSide, (const real*)m.sJ,
-                                                   (const real*)m.Utv, U, dU, Ut, (real*)m.Wf, m.xsol, rk, t, src,
-                                                   m.K, m.S, ops, ph, m.status);
+    FLEXI_SURF(1, 1);
+#undef FLEXI_SURF
   return cudaGetLastError();
 }
 
