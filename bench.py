@@ -50,7 +50,7 @@ def peaks():
 # capture time; reported only while the sources are unchanged (else null).
 KERNEL_SOURCES = ["paper_1910_02858_gb300/csrc/k_dg.cuh", "paper_1910_02858_gb300/csrc/dg_common.cuh",
                   "paper_1910_02858_gb300/csrc/k_tc.cuh"]
-NCU_TRAFFIC = {("fp64", "fe9c8b798b0d4267"): 573841408, ("fp32", "fe9c8b798b0d4267"): 266458112}
+NCU_TRAFFIC = {("fp64", "d5ddc5e3a099b0ba"): 573887744, ("fp32", "d5ddc5e3a099b0ba"): 266877440}
 
 
 def kernel_source_hash(texts=None) -> str:
