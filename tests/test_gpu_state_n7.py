@@ -115,3 +115,16 @@ def test_c2_full_size_ten_steps():
     err = rel_per_var(Ug, ref)
     print("c2 16^3 dt", dt, "rel L2 per variable", ["%.2e" % e for e in err])
     assert max(err) <= TOL, err
+
+
+def test_n5_ten_steps_precision_form_order():
+    """N = 5, the order of the precision form's 32^3 workload, whose FP32 errors are
+    measured against this FP64 path: Taylor-Green on a reoriented 3x2x2 Gauss mesh (the
+    n = 6 kernel instances), ten steps at CFL 0.9, 1e-12 per conserved variable."""
+    N = 5
+    mesh = wl.box_mesh((3, 2, 2), Ngeo=1, reorient_seed=9)
+    U0 = wl.taylor_green(mesh.node_coords(N, 0))
+    Ug, ref, dt = _run_both(mesh, N, 0, U0, 10)
+    err = rel_per_var(Ug, ref)
+    print("N5 tgv_lg_3x2x2 dt", dt, "rel L2 per variable", ["%.2e" % e for e in err])
+    assert max(err) <= TOL, err
