@@ -50,7 +50,7 @@ def peaks():
 # capture time; reported only while the sources are unchanged (else null).
 KERNEL_SOURCES = ["paper_1910_02858_gb300/csrc/k_dg.cuh", "paper_1910_02858_gb300/csrc/dg_common.cuh",
                   "paper_1910_02858_gb300/csrc/k_tc.cuh"]
-NCU_TRAFFIC = {("fp64", "d5ddc5e3a099b0ba"): 573887744, ("fp32", "d5ddc5e3a099b0ba"): 266877440}
+NCU_TRAFFIC = {("fp64", "aa886da54308592e"): 573897984, ("fp32", "aa886da54308592e"): 266756864}
 
 
 def kernel_source_hash(texts=None) -> str:

@@ -611,6 +611,43 @@ __device__ __forceinline__ void lift_vol_body(
       const int mpq = orient_pq(es_orient(es), n - 1, p, q);
       Gf[((size_t)(es_slave(es) * S + es_side(es)) * 15 + c) * n2 + mpq] = val;
     }
+  } else if constexpr (NE == 1) {
+    // one pass per line of direction l gives the values on both faces -l and +l; the face
+    // node of the line has (p, q) = its free indices.  With one element per CTA (n^3
+    // threads, n^2 lines) every task of a thread has the same line, tid mod n^2: its two
+    // faces' slots and master-frame nodes are read once per direction, and the tasks differ
+    // only in the component c = tid / n^2 + k n.
+    constexpr int P = C::P;
+    const int line = tid % n2, c0 = tid / n2;
+    const int p = line % n, q = line / n;
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+      const int stride = l == 0 ? 1 : (l == 1 ? P : P * n);
+      const int base = l == 0 ? P * line : (l == 1 ? p + P * n * q : p + P * q);
+      real* gm_out = Gf + (size_t)sSlot[2 * l] * 15 * n2 + sMpq[(2 * l) * n2 + line];
+      real* gp_out = Gf + (size_t)sSlot[2 * l + 1] * 15 * n2 + sMpq[(2 * l + 1) * n2 + line];
+      for (int c = c0; c < 15; c += T / n2) {
+        const real* b = sbuf + c * n3p + base;
+        real gm = real(0), gp = real(0);
+        if (LGL) {
+          gm = b[0];
+          gp = b[(n - 1) * stride];
+        } else {
+#pragma unroll
+          for (int a = 0; a < n; ++a) {
+            const real x = b[a * stride];
+            gm += ops.lm[a] * x;
+            gp += ops.lp[a] * x;
+          }
+        }
+        if constexpr (BR2) {
+          gm += br2_own(0, 2 * l, c, p, q);
+          gp += br2_own(0, 2 * l + 1, c, p, q);
+        }
+        gm_out[c * n2] = gm;
+        gp_out[c * n2] = gp;
+      }
+    }
   } else {
     // one pass per line of direction l gives the values on both faces -l and +l;
     // the face node of the line has (p, q) = its free indices
