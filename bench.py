@@ -50,7 +50,7 @@ def peaks():
 # capture time; reported only while the sources are unchanged (else null).
 KERNEL_SOURCES = ["paper_1910_02858_gb300/csrc/k_dg.cuh", "paper_1910_02858_gb300/csrc/dg_common.cuh",
                   "paper_1910_02858_gb300/csrc/k_tc.cuh"]
-NCU_TRAFFIC = {("fp64", "aa886da54308592e"): 573897984, ("fp32", "aa886da54308592e"): 266756864}
+NCU_TRAFFIC = {("fp64", "98f866c185623c76"): 575194368, ("fp32", "98f866c185623c76"): 266848256}
 
 
 def kernel_source_hash(texts=None) -> str:
@@ -311,6 +311,9 @@ def main():
     ap.add_argument("--nelem", type=int, default=16,
                     help="elements per direction of the timed Taylor-Green mesh (16: the headline workload; "
                          "smaller meshes for profiler captures)")
+    ap.add_argument("--case", default=None, choices=["c1"],
+                    help="time only the small C1 case (4^3 elements, N = 3 Gauss-Lobatto, Roe, FP64): "
+                         "--warmup steps, then --steps steps replayed from the CUDA graph; one JSON line")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -344,6 +347,9 @@ def main():
     if dist is not None:
         dist.barrier()
     F.lib()
+    if args.case == "c1":
+        print(json.dumps(c1_case(args, dev, F, wl, Solver, SolverConfig, torch)))
+        return 0
 
     N = 7
     mesh = wl.box_mesh((args.nelem,) * 3, Ngeo=1)
@@ -739,6 +745,29 @@ def small_cases_pid(dev, F, wl, Solver, SolverConfig, torch):
         finally:
             s.close()
     return res
+
+
+def c1_case(args, dev, F, wl, Solver, SolverConfig, torch):
+    """C1 alone (Taylor-Green, 4^3 periodic elements, N = 3 Gauss-Lobatto, Roe, FP64,
+    dt = 1e-4): args.warmup steps, then args.steps steps of flexi_rk_run (CUDA-graph
+    replay), event-timed on the launching stream; PID in ns per DOF and RK stage."""
+    mesh = wl.box_mesh((4,) * 3, Ngeo=1)
+    s = Solver(SolverConfig(N=3, node_type=1, riemann=F.RIEMANN_ROE), mesh.coords, mesh.conn, device=dev)
+    try:
+        U = torch.tensor(wl.taylor_green(mesh.node_coords(3, 1)), device=dev)
+        dof = s.query(F.Q_DOF)
+        s.run(U, args.warmup, 1e-4)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        s.run(U, args.steps, 1e-4)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        pid = e0.elapsed_time(e1) * 1e6 / (args.steps * NSTAGES * dof)
+        return {"case": "c1_4^3_N3_lgl_roe_fp64", "dof": dof, "steps": args.steps, "warmup": args.warmup,
+                "pid_graph": pid, "unit": "ns/DOF/RK-stage"}
+    finally:
+        s.close()
 
 
 def mortar_pid(dt, dev, F, wl, Solver, SolverConfig, torch):

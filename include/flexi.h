@@ -164,12 +164,15 @@ flexi_status flexi_rhs(flexi_ctx *ctx, const void *U, void *Ut, double t, void *
  * U, dU: device, updated in place (dU is multiplied by A_1 = 0 first). */
 flexi_status flexi_rk_step(flexi_ctx *ctx, void *U, void *dU, double t, double dt, void *stream);
 
-/* nsteps calls of flexi_rk_step (times t0 + s dt), enqueued on `stream`.  When one
- * step does not depend on t (no source term, no exact-state boundary with the
- * time-dependent manufactured state), stream is not the legacy NULL stream and
- * kernel timing is off, the first step runs eagerly and the rest replay a CUDA
- * graph of one step, captured once per (U, dU, dt, stream) and kept in the
- * context (same kernels in the same order, so the results are identical).
+/* nsteps steps of flexi_rk_step (times t0 + s dt), enqueued on `stream`.  The last
+ * stage of each step but the last also writes the face states of the new U, so
+ * that only the first step prolongs U (the same arithmetic: the results equal
+ * those of nsteps flexi_rk_step calls bit for bit).  When one step does not
+ * depend on t (no source term, no exact-state boundary with the time-dependent
+ * manufactured state), stream is not the legacy NULL stream, kernel timing is off
+ * and nsteps > 1, the first step runs eagerly and the rest replay a CUDA graph of
+ * one step, captured once per (U, dU, dt, stream) and kept in the context; a later
+ * call that reuses it prolongs the caller's U first.
  * U, dU: device, updated in place. */
 flexi_status flexi_rk_run(flexi_ctx *ctx, void *U, void *dU, int nsteps, double t0, double dt, void *stream);
 
@@ -198,8 +201,9 @@ flexi_status flexi_rhs_adjoint(flexi_ctx *ctx, const void *U, const void *lam, v
                                void *stream);
 
 /* End-to-end convenience call on HOST memory: copies U_host (pinned or pageable,
- * layout as above) to the device state, runs nsteps flexi_rk_step calls from
- * t0 with step dt, and copies the result back into U_host.  Synchronous. */
+ * layout as above) to the device state, runs nsteps steps from t0 with step dt as
+ * flexi_rk_run does without a graph, and copies the result back into U_host.
+ * Synchronous. */
 flexi_status flexi_rk_run_host(flexi_ctx *ctx, void *U_host, int nsteps, double t0, double dt, void *stream);
 
 /* Global FP64 reductions (Sec. 5.3: the only all-to-all operation is the global

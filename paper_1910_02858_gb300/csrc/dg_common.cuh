@@ -168,6 +168,13 @@ template <>
 __device__ __forceinline__ float dg_sqrt<float>(float x) { return sqrtf(x); }
 
 template <typename real>
+__device__ __forceinline__ real dg_rsqrt(real x);
+template <>
+__device__ __forceinline__ double dg_rsqrt<double>(double x) { return rsqrt(x); }
+template <>
+__device__ __forceinline__ float dg_rsqrt<float>(float x) { return rsqrtf(x); }
+
+template <typename real>
 __device__ __forceinline__ real dg_abs(real x) { return x < real(0) ? -x : x; }
 
 // a * b + c in one rounding (one FP64 pipe slot for two flops in the FP64 form;
@@ -262,10 +269,14 @@ __device__ __forceinline__ void riemann_hllc(const real WL[NV], const real WR[NV
   riemann_hllc(WL, WR, real(1) / WL[0], real(1) / WR[0], n, ph, f);
 }
 
-// Roe flux (5-wave, frame-free); smooth != 0: Harten-type smoothing of |lambda|
+// Roe flux (5-wave, frame-free); smooth != 0: Harten-type smoothing of |lambda| (below
+// delta = 0.1 c, (lambda^2 + delta^2) / (2 delta)).  Written as f = (S - D) / 2: the central
+// part S = F(W_L).n + F(W_R).n and the dissipation D = sum_k |lambda_k| alpha_k r_k with
+// Roe averages weighted by sqrt(rho); irL, irR = 1 / rho.  The two parts are independent, so
+// a kernel with few face nodes per SM computes them in separate warps.
 template <typename real>
-__device__ __forceinline__ void riemann_roe(const real WL[NV], const real WR[NV], const real n[3],
-                                            const Phys<real>& ph, bool smooth, real f[NV]) {
+__device__ __forceinline__ void roe_central(const real WL[NV], const real WR[NV], const real n[3],
+                                            const Phys<real>& ph, real S[NV]) {
   const real q2L = WL[1] * WL[1] + WL[2] * WL[2] + WL[3] * WL[3];
   const real q2R = WR[1] * WR[1] + WR[2] * WR[2] + WR[3] * WR[3];
   const real EL = WL[4] * ph.inv_gm1 + real(0.5) * WL[0] * q2L;
@@ -275,18 +286,32 @@ __device__ __forceinline__ void riemann_roe(const real WL[NV], const real WR[NV]
   real FL[NV], FR[NV];
   euler_normal(WL, EL, uL, n, FL);
   euler_normal(WR, ER, uR, n, FR);
-  const real sL = dg_sqrt(WL[0]), sR = dg_sqrt(WR[0]);
-  const real iws = real(1) / (sL + sR);
-  const real HL = (EL + WL[4]) / WL[0], HR = (ER + WR[4]) / WR[0];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) S[v] = FL[v] + FR[v];
+}
+
+template <typename real>
+__device__ __forceinline__ void roe_dissipation(const real WL[NV], const real WR[NV], const real irL, const real irR,
+                                                const real n[3], const Phys<real>& ph, bool smooth, real D[NV]) {
+  const real q2L = WL[1] * WL[1] + WL[2] * WL[2] + WL[3] * WL[3];
+  const real q2R = WR[1] * WR[1] + WR[2] * WR[2] + WR[3] * WR[3];
+  const real EL = WL[4] * ph.inv_gm1 + real(0.5) * WL[0] * q2L;
+  const real ER = WR[4] * ph.inv_gm1 + real(0.5) * WR[0] * q2R;
+  // Roe averages (sqrt(rho_L) a_L + sqrt(rho_R) a_R) / (sqrt(rho_L) + sqrt(rho_R)) written
+  // with r = sqrt(rho_R / rho_L) as (a_L + r a_R) / (1 + r), and sqrt(rho_L rho_R) = rho_L r
+  const real r = dg_sqrt(WR[0] * irL);
+  const real iw = real(1) / (real(1) + r);
+  const real HL = (EL + WL[4]) * irL, HR = (ER + WR[4]) * irR;
   real vel[3];
 #pragma unroll
-  for (int c = 0; c < 3; ++c) vel[c] = (sL * WL[1 + c] + sR * WR[1 + c]) * iws;
-  const real H = (sL * HL + sR * HR) * iws;
+  for (int c = 0; c < 3; ++c) vel[c] = dg_fma(r, WR[1 + c], WL[1 + c]) * iw;
+  const real H = dg_fma(r, HR, HL) * iw;
   const real q2 = vel[0] * vel[0] + vel[1] * vel[1] + vel[2] * vel[2];
   const real c2 = ph.gm1 * (H - real(0.5) * q2);
-  const real c = dg_sqrt(c2);
-  const real ic2 = real(1) / c2;
-  const real rho = sL * sR;
+  const real ic = dg_rsqrt(c2);  // c = c2 / sqrt(c2) and 1 / c2 from one reciprocal square root
+  const real c = c2 * ic;
+  const real ic2 = ic * ic;
+  const real rho = WL[0] * r;
   const real un = vel[0] * n[0] + vel[1] * n[1] + vel[2] * n[2];
   const real dp = WR[4] - WL[4];
   real dv[3];
@@ -299,7 +324,7 @@ __device__ __forceinline__ void riemann_roe(const real WL[NV], const real WR[NV]
   real l1 = dg_abs(un - c), l2 = dg_abs(un), l5 = dg_abs(un + c);
   if (smooth) {
     const real del = real(0.1) * c;
-    const real ih = real(0.5) / del;
+    const real ih = real(5) * ic;  // 1 / (2 del)
     if (l1 < del) l1 = (l1 * l1 + del * del) * ih;
     if (l2 < del) l2 = (l2 * l2 + del * del) * ih;
     if (l5 < del) l5 = (l5 * l5 + del * del) * ih;
@@ -309,12 +334,21 @@ __device__ __forceinline__ void riemann_roe(const real WL[NV], const real WR[NV]
 #pragma unroll
   for (int k = 0; k < 3; ++k) dvt[k] = dv[k] - dun * n[k];
   const real vdvt = vel[0] * dvt[0] + vel[1] * dvt[1] + vel[2] * dvt[2];
-  f[0] = real(0.5) * (FL[0] + FR[0] - (w1 + w5 + w2));
+  D[0] = w1 + w5 + w2;
 #pragma unroll
   for (int k = 0; k < 3; ++k)
-    f[1 + k] = real(0.5) * (FL[1 + k] + FR[1 + k] -
-                            (w1 * (vel[k] - c * n[k]) + w5 * (vel[k] + c * n[k]) + w2 * vel[k] + wt * dvt[k]));
-  f[4] = real(0.5) * (FL[4] + FR[4] - (w1 * (H - un * c) + w5 * (H + un * c) + w2 * real(0.5) * q2 + wt * vdvt));
+    D[1 + k] = w1 * (vel[k] - c * n[k]) + w5 * (vel[k] + c * n[k]) + w2 * vel[k] + wt * dvt[k];
+  D[4] = w1 * (H - un * c) + w5 * (H + un * c) + w2 * real(0.5) * q2 + wt * vdvt;
+}
+
+template <typename real>
+__device__ __forceinline__ void riemann_roe(const real WL[NV], const real WR[NV], const real irL, const real irR,
+                                            const real n[3], const Phys<real>& ph, bool smooth, real f[NV]) {
+  real S[NV], D[NV];
+  roe_central(WL, WR, n, ph, S);
+  roe_dissipation(WL, WR, irL, irR, n, ph, smooth, D);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) f[v] = real(0.5) * (S[v] - D[v]);
 }
 
 // Rusanov (local Lax-Friedrichs): central flux minus lambda_max/2 times the jump
@@ -408,7 +442,7 @@ __device__ __forceinline__ void riemann_kind(const real WL[NV], const real WR[NV
   else if constexpr (RS == 4)
     riemann_ec(WL, WR, n, ph, f);
   else
-    riemann_roe(WL, WR, n, ph, ph.riemann == 2, f);
+    riemann_roe(WL, WR, irL, irR, n, ph, ph.riemann == 2, f);
 }
 
 template <typename real>
@@ -421,7 +455,7 @@ __device__ __forceinline__ void riemann(const real WL[NV], const real WR[NV], co
   else if (ph.riemann == 4)
     riemann_ec(WL, WR, n, ph, f);
   else
-    riemann_roe(WL, WR, n, ph, ph.riemann == 2, f);
+    riemann_roe(WL, WR, real(1) / WL[0], real(1) / WR[0], n, ph, ph.riemann == 2, f);
 }
 
 // exact states (Dirichlet data) -- conservative variables at x, time t

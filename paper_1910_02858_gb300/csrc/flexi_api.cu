@@ -56,6 +56,13 @@ struct flexi_ctx {
   MortarOps<double> mops64{};
   MortarOps<float> mops32{};
   int nMortar = 0;
+  // small FP64 meshes (n = 4, fewer elements than SMs, BR1, no mortars): the face fluxes
+  // and the surface/RK kernel of an RK stage run as one kernel (k_surf_face), which reads
+  // the face states of one buffer and writes those of the new U into another; m.Wf and the
+  // two extra buffers take turns so that every step uses the same pattern (a CUDA graph of
+  // one step stays valid)
+  bool fused = false;
+  void *WfA = nullptr, *WfB = nullptr;
   // CUDA graph of one RK step (flexi_rk_run), keyed by the buffers, dt and stream
   cudaGraphExec_t graph = nullptr;
   const void *gU = nullptr, *gdU = nullptr;
@@ -155,8 +162,10 @@ template <>
 const Phys<float>& ph_of<float>(const flexi_ctx* c) { return c->ph32; }
 
 // one evaluation of the operator up to (and excluding) the surface kernel
+// face = false: without the face fluxes (k_surf_face computes them)
 template <typename real>
-flexi_status stage_front(flexi_ctx* c, const real* U, double t, bool prolong, int store_grad, cudaStream_t st) {
+flexi_status stage_front(flexi_ctx* c, const real* U, double t, bool prolong, int store_grad, cudaStream_t st,
+                         bool face = true) {
   const Ops<real>& ops = ops_of<real>(c);
   const Phys<real>& ph = ph_of<real>(c);
   if (prolong) {
@@ -179,7 +188,7 @@ flexi_status stage_front(flexi_ctx* c, const real* U, double t, bool prolong, in
     Prof pr(c, KC_OTHER, st);
     CK(launch_mortar_grad<real>(c->m, mo_of<real>(c), ph, st));
   }
-  {
+  if (face) {
     Prof pr(c, KC_FACE, st);
     CK(launch_face<real>(c->m, ph, st));
   }
@@ -200,15 +209,55 @@ flexi_status do_rhs(flexi_ctx* c, const real* U, real* Ut, double t, cudaStream_
   return FLEXI_OK;
 }
 
+// faces_ready: the face states of U are already in place (written by the last stage of
+// the previous step); prolong_last: the last stage also writes the face states of the new
+// U for a following step (the same faces_from_volume arithmetic as the prolongation)
+// fused stages (c->fused): stage k reads the face states of buffer in(k) and writes those of
+// the new U into out(k): C -> B, B -> A, A -> B, B -> A, A -> C with C = m.Wf, so that a
+// step starts and ends on m.Wf
 template <typename real>
-flexi_status do_rk_step(flexi_ctx* c, real* U, real* dU, double t, double dt, real* stages, cudaStream_t st) {
+flexi_status do_rk_step_fused(flexi_ctx* c, real* U, real* dU, double t, double dt, real* stages, cudaStream_t st,
+                              bool faces_ready, bool prolong_last) {
+  if constexpr (sizeof(real) == 8) {
+    void* const WfC = c->m.Wf;
+    const size_t nU = (size_t)c->K * NV * c->n3;
+    flexi_status res = FLEXI_OK;
+    for (int k = 0; k < 5 && res == FLEXI_OK; ++k) {
+      void* const win = k == 0 ? WfC : ((k & 1) ? c->WfB : c->WfA);
+      void* const wout = k == 4 ? WfC : ((k & 1) ? c->WfA : c->WfB);
+      const double tk = t + RK_C[k] * dt;
+      if (stages != nullptr &&
+          cudaMemcpyAsync(stages + k * nU, U, nU * sizeof(real), cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
+        res = FLEXI_ECUDA;
+        break;
+      }
+      c->m.Wf = win;  // prolongation, boundary states and the lifting use the stage's buffer
+      res = stage_front<real>(c, U, tk, k == 0 && !faces_ready, 0, st, false);
+      if (res != FLEXI_OK) break;
+      RkStage<real> rk{(real)RK_A[k], (real)RK_B[k], (real)dt, (k < 4 || prolong_last) ? 1 : 0};
+      Prof pr(c, KC_SURF, st);
+      if (launch_surf_face(c->m, win, wout, U, dU, rk, tk, c->src, ops_of<real>(c), ph_of<real>(c), st) !=
+          cudaSuccess)
+        res = FLEXI_ECUDA;
+    }
+    c->m.Wf = WfC;
+    return res;
+  } else {
+    return FLEXI_EUNSUPPORTED;
+  }
+}
+
+template <typename real>
+flexi_status do_rk_step(flexi_ctx* c, real* U, real* dU, double t, double dt, real* stages, cudaStream_t st,
+                        bool faces_ready = false, bool prolong_last = false) {
+  if (c->fused) return do_rk_step_fused<real>(c, U, dU, t, dt, stages, st, faces_ready, prolong_last);
   const size_t nU = (size_t)c->K * NV * c->n3;
   for (int k = 0; k < 5; ++k) {
     const double tk = t + RK_C[k] * dt;
     if (stages != nullptr) CK(cudaMemcpyAsync(stages + k * nU, U, nU * sizeof(real), cudaMemcpyDeviceToDevice, st));
-    flexi_status s = stage_front<real>(c, U, tk, k == 0, 0, st);
+    flexi_status s = stage_front<real>(c, U, tk, k == 0 && !faces_ready, 0, st);
     if (s != FLEXI_OK) return s;
-    RkStage<real> rk{(real)RK_A[k], (real)RK_B[k], (real)dt, k < 4 ? 1 : 0};
+    RkStage<real> rk{(real)RK_A[k], (real)RK_B[k], (real)dt, (k < 4 || prolong_last) ? 1 : 0};
     Prof pr(c, KC_SURF, st);
     CK(launch_surf<real>(c->m, 1, U, dU, nullptr, rk, tk, c->src, ops_of<real>(c), ph_of<real>(c), st));
   }
@@ -597,6 +646,14 @@ flexi_status mesh_init_impl(flexi_ctx* c, const flexi_params* p, int K, const do
   AL(Us, (size_t)K * NV * n3 * rs);
   AL(dUs, (size_t)K * NV * n3 * rs);
   c->m.Wf = Wf; c->m.Gf = Gf; c->m.Ff = Ff; c->m.Utv = Utv;
+  c->fused = c->fp64 && !c->m.br2 && c->nMortar == 0 && n == 4 && K < c->m.nsm;
+  if (c->fused) {
+    unsigned char *WfA, *WfB;
+    AL(WfA, 2 * (size_t)S * NV * n2 * rs);
+    AL(WfB, 2 * (size_t)S * NV * n2 * rs);
+    c->WfA = WfA;
+    c->WfB = WfB;
+  }
   c->Ustate = Us; c->dUstate = dUs;
   c->red_blocks = std::max(1, std::min(4 * 152, (int)(((size_t)K * n3 + 255) / 256)));
   AL(c->partial, (size_t)c->red_blocks * kReduceQuantities);
@@ -832,25 +889,46 @@ static bool autonomous(const flexi_ctx* c) {
   return true;
 }
 
+// one RK step of either precision (see do_rk_step for faces_ready and prolong_last)
+static flexi_status rk_step_any(flexi_ctx* c, void* U, void* dU, double t, double dt, cudaStream_t st,
+                                bool faces_ready, bool prolong_last) {
+  return c->fp64 ? do_rk_step<double>(c, (double*)U, (double*)dU, t, dt, nullptr, st, faces_ready, prolong_last)
+                 : do_rk_step<float>(c, (float*)U, (float*)dU, t, dt, nullptr, st, faces_ready, prolong_last);
+}
+
+// face states of U (the prolongation that opens a step)
+static flexi_status prolong_any(flexi_ctx* c, const void* U, cudaStream_t st) {
+  Prof pr(c, KC_PROLONG, st);
+  if (c->fp64) {
+    CK(launch_prolong<double>(c->m, (const double*)U, ops_of<double>(c), ph_of<double>(c), st));
+  } else {
+    CK(launch_prolong<float>(c->m, (const float*)U, ops_of<float>(c), ph_of<float>(c), st));
+  }
+  return FLEXI_OK;
+}
+
 flexi_status flexi_rk_run(flexi_ctx* c, void* U, void* dU, int nsteps, double t0, double dt, void* stream) {
   if (c == nullptr || U == nullptr || dU == nullptr || nsteps < 0) return FLEXI_EINVAL;
   if (!on_ctx_device(c)) return FLEXI_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
+  if (nsteps == 0) return FLEXI_OK;
+  // consecutive steps hand over their face states: the last stage of a step writes those
+  // of the next step's U, so only the call's first step prolongs U itself
   const bool use_graph = st != nullptr && !c->prof && autonomous(c) && nsteps > 1;
+  if (!use_graph) {
+    for (int s = 0; s < nsteps; ++s) {
+      const flexi_status r = rk_step_any(c, U, dU, t0 + s * dt, dt, st, s > 0, s + 1 < nsteps);
+      if (r != FLEXI_OK) return r;
+    }
+    return FLEXI_OK;
+  }
   int s = 0;
-  if (!use_graph || c->graph == nullptr || c->gU != U || c->gdU != dU || c->gdt != dt || c->gst != st) {
+  if (c->graph == nullptr || c->gU != U || c->gdU != dU || c->gdt != dt || c->gst != st) {
     // one eager step (also performs every one-time kernel attribute setting outside a capture)
-    if (nsteps > 0) {
-      const flexi_status r = flexi_rk_step(c, U, dU, t0, dt, stream);
+    {
+      const flexi_status r = rk_step_any(c, U, dU, t0, dt, st, false, true);
       if (r != FLEXI_OK) return r;
       s = 1;
-    }
-    if (!use_graph) {
-      for (; s < nsteps; ++s) {
-        const flexi_status r = flexi_rk_step(c, U, dU, t0 + s * dt, dt, stream);
-        if (r != FLEXI_OK) return r;
-      }
-      return FLEXI_OK;
     }
     if (c->graph) {
       cudaGraphExecDestroy(c->graph);
@@ -858,7 +936,8 @@ flexi_status flexi_rk_run(flexi_ctx* c, void* U, void* dU, int nsteps, double t0
     }
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-    const flexi_status r = flexi_rk_step(c, U, dU, t0, dt, stream);
+    // the captured step takes its face states from the step before it and leaves the next one's
+    const flexi_status r = rk_step_any(c, U, dU, t0, dt, st, true, true);
     const cudaError_t e = cudaStreamEndCapture(st, &g);
     if (r != FLEXI_OK || e != cudaSuccess) {
       if (g) cudaGraphDestroy(g);
@@ -875,6 +954,9 @@ flexi_status flexi_rk_run(flexi_ctx* c, void* U, void* dU, int nsteps, double t0
     c->gdU = dU;
     c->gdt = dt;
     c->gst = st;
+  } else {
+    const flexi_status r = prolong_any(c, U, st);  // the face states of the caller's U
+    if (r != FLEXI_OK) return r;
   }
   for (; s < nsteps; ++s) CK(cudaGraphLaunch(c->graph, st));
   return FLEXI_OK;
@@ -888,7 +970,7 @@ flexi_status flexi_rk_run_host(flexi_ctx* c, void* U_host, int nsteps, double t0
   CK(cudaMemcpyAsync(c->Ustate, U_host, bytes, cudaMemcpyHostToDevice, st));
   CK(cudaMemsetAsync(c->dUstate, 0, bytes, st));
   for (int s = 0; s < nsteps; ++s) {
-    const flexi_status r = flexi_rk_step(c, c->Ustate, c->dUstate, t0 + s * dt, dt, stream);
+    const flexi_status r = rk_step_any(c, c->Ustate, c->dUstate, t0 + s * dt, dt, st, s > 0, s + 1 < nsteps);
     if (r != FLEXI_OK) return r;
   }
   CK(cudaMemcpyAsync(U_host, c->Ustate, bytes, cudaMemcpyDeviceToHost, st));

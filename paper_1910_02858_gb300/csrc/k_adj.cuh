@@ -310,6 +310,15 @@ __device__ __forceinline__ Dual<r> dg_sqrt(Dual<r> x) {
   return Dual<r>(s, x.d / (r(2) * s));
 }
 template <typename r>
+__device__ __forceinline__ Dual<r> dg_rsqrt(Dual<r> x) {  // d(x^-1/2) = -x^-3/2 dx / 2
+  const r s = dg_rsqrt(x.v);
+  return Dual<r>(s, r(-0.5) * x.d * s * s * s);
+}
+template <typename r>
+__device__ __forceinline__ Dual<r> dg_fma(Dual<r> a, Dual<r> b, Dual<r> c) {
+  return a * b + c;
+}
+template <typename r>
 __device__ __forceinline__ Dual<r> dg_log(Dual<r> x) {
   return Dual<r>(dg_log(x.v), x.d / x.v);
 }

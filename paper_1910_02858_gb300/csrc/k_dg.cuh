@@ -1093,6 +1093,296 @@ __global__ void __launch_bounds__(3 * n * n * n) k_lift_vol_g3(
   }
 }
 
+// Thread-block cluster primitives (sm_90 and later): the CTA's rank in its cluster; a
+// barrier over every thread of the cluster whose arrive releases and whose wait acquires
+// this CTA's prior shared-memory accesses (split in two where the wait can come later);
+// and the generic address of the same shared-memory location in another CTA of the
+// cluster (distributed shared memory), readable with ordinary loads.
+__device__ __forceinline__ unsigned cluster_ctarank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
+__device__ __forceinline__ void cluster_barrier() {
+  cluster_arrive();
+  cluster_wait();
+}
+template <typename T>
+__device__ __forceinline__ const T* cluster_peer(const T* p, unsigned rank) {
+  unsigned long long a;
+  asm volatile("mapa.u64 %0, %1, %2;" : "=l"(a) : "l"(reinterpret_cast<unsigned long long>(p)), "r"(rank));
+  return reinterpret_cast<const T*>(a);
+}
+
+// a2-a4, a6, a7 for FP64 meshes with at most half as many elements as SMs (n = 4; standard
+// form, BR1).  On such meshes each thread's chain of dependent instructions sets the time,
+// not the throughput of any unit (on GB300 an FP64 warp instruction holds its SM
+// sub-partition for 64 clocks however few of its lanes are active), so an element's work is
+// cut finely.  One cluster of two CTAs per element: CTA r holds the nodes with k in
+// [r n/2, (r + 1) n/2), and one warp per pair (g, v) of a direction (or gradient component) g
+// and a variable v runs over the CTA's n^3/2 = 32 nodes, 15 warps in all.  Warp (g, v) forms
+// the lifting fields Ja^l_g W_v, sweeps them into dW_v/dx_g, evaluates the flux component
+// (F_g)_v, then the contravariant flux component of reference direction g and its D_hat
+// sweep.  Lines along i and j lie inside a half.  What a half needs of the other one is
+// copied from the other CTA's shared memory after a cluster barrier: the lifting fields of
+// the third reference direction, the contravariant fluxes of that direction and, on Gauss
+// nodes, the gradients that the k faces interpolate.  Each copy fills positions that the
+// copying CTA never writes itself, while the other CTA reads only its own positions, and
+// every buffer that the other CTA reads stays unchanged until the next cluster barrier.
+// The face gradients of a face node come from the half that holds its volume nodes (faces
+// +-i and +-j: the half of q, face -k: CTA 0, face +k: CTA 1).  The expressions per node
+// are those of k_lift_vol_g3 (cons_to_prim, node_sweep3, flux_total, the same face terms,
+// contravariant products and sums in the same order).
+template <int n, bool LGL>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(15 * n * n * n / 2) k_lift_vol_c2(
+    const double* __restrict__ U, const double* __restrict__ Ja, const double* __restrict__ sJ,
+    const double* __restrict__ Wf, const double* __restrict__ fgeo, const int* __restrict__ elemSide,
+    double* __restrict__ Gf, double* __restrict__ Utv, double* __restrict__ Gvol, int K, int S, int bigBase,
+    const double* __restrict__ QB, Ops<double> ops, Phys<double> ph) {
+  static_assert(n * n * n / 2 == 32, "one warp per (g, v) over the 32 nodes of a half element");
+  using real = double;
+  constexpr int n2 = n * n, n3 = n2 * n, h3 = n3 / 2, hk = n / 2, T = 15 * h3, n3p = Cfg<n>::n3p;
+  static_assert(15 * n3p <= 6 * 15 * n2, "the gradients fit the surface-term buffer");
+  __shared__ real sbuf[3 * 15 * n3p];  // lifting fields; then fluxes and partial sums (region 1), contravariant fluxes (region 2)
+  __shared__ real sQ[6 * 15 * n2];     // BR1 surface terms [6][15][n2]; then the gradients [15][n3p]
+  __shared__ real sW[NV * n3p];        // primitive variables of this half's nodes
+  __shared__ real sOp[n2 + 4 * n];
+  __shared__ int sES[6], sSlot[6], sMpq[6 * n2];
+  const int tid = threadIdx.x;
+  const unsigned r = cluster_ctarank();
+  const int kb = (int)(r ^ 1u) * hk;  // first k of the other half
+  const int wp = tid >> 5, ln = tid & 31;
+  const int g = wp / NV, v = wp - g * NV;  // warp-uniform
+  const int e = blockIdx.x >> 1;           // grid = 2 K, clusters of two consecutive CTAs
+  const int i = ln % n, j = (ln / n) % n, k = (int)r * hk + ln / n2;
+  const int node = i + n * (j + n * k);
+  const int pn = pidx<n>(i, j, k);
+  load_ops<real, n>(sOp, ops, tid, T);
+  if (tid < 6) {
+    const int es = elemSide[(size_t)e * 6 + tid];
+    sES[tid] = es;
+    sSlot[tid] = es_slave(es) * S + es_side(es);
+  }
+  real Uo[NV];
+#pragma unroll
+  for (int c = 0; c < NV; ++c) Uo[c] = U[((size_t)e * NV + c) * n3 + node];
+  real col[3], row[3];  // Ja^l_g (l = 0..2) and Ja^g_d (d = 0..2)
+#pragma unroll
+  for (int l = 0; l < 3; ++l) {
+    col[l] = Ja[((size_t)e * 9 + l * 3 + g) * n3 + node];
+    row[l] = Ja[((size_t)e * 9 + g * 3 + l) * n3 + node];
+  }
+  const real sj = sJ[(size_t)e * n3 + node];
+  if (g == 0) {  // W_v as cons_to_prim forms it
+    const real ir = real(1) / Uo[0];
+    const real u = Uo[1] * ir, vv = Uo[2] * ir, w = Uo[3] * ir;
+    real Wv = Uo[0];
+    if (v == 1) Wv = u;
+    if (v == 2) Wv = vv;
+    if (v == 3) Wv = w;
+    if (v == 4) Wv = ph.gm1 * (Uo[4] - real(0.5) * (Uo[1] * u + Uo[2] * vv + Uo[3] * w));
+    sW[v * n3p + pn] = Wv;
+  }
+  __syncthreads();
+  // BR1 surface terms of the face nodes that this half reads, one thread per (variable,
+  // face node) with the expressions of br1_surface_terms: faces 0-3 with q in
+  // [r n/2, (r + 1) n/2), then face 4 + r (Gauss-Lobatto: only the nodes on a face read it)
+  // or both k faces (Gauss: every node reads both)
+  constexpr int nIJq = 4 * (n2 / 2), nKf = LGL ? n2 : 2 * n2, nQ = nIJq + nKf;
+  for (int it = tid; it < NV * nQ; it += T) {
+    const int c = it / nQ, f = it - c * nQ;
+    int s, pq;
+    if (f < nIJq) {
+      s = f / (n2 / 2);
+      const int m = f - s * (n2 / 2);
+      pq = m % n + n * ((int)r * hk + m / n);
+    } else {
+      const int fk = f - nIJq;
+      s = LGL ? 4 + (int)r : 4 + fk / n2;
+      pq = fk % n2;
+    }
+    const int es = sES[s];
+    const int side = es_side(es);
+    const int mpq = orient_pq(es_orient(es), n - 1, pq % n, pq / n);
+    if (c == 0) sMpq[s * n2 + pq] = mpq;
+    const real* gq = fgeo + ((size_t)side * 4) * n2 + mpq;
+    const real sc = es_slave(es) ? -gq[3 * n2] : gq[3 * n2];
+    const real nd[3] = {gq[0] * sc, gq[n2] * sc, gq[2 * n2] * sc};
+    real* Q = sQ + (s * 15 + c * 3) * n2 + pq;
+    if (side >= bigBase) {
+      const real* qb = QB + ((size_t)(side - bigBase) * 15 + c * 3) * n2 + mpq;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) Q[d * n2] = qb[d * n2];
+    } else {
+      const real ws = real(0.5) * (Wf[((size_t)side * NV + c) * n2 + mpq] + Wf[((size_t)(S + side) * NV + c) * n2 + mpq]);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) Q[d * n2] = ws * nd[d];
+    }
+  }
+  real* myb = sbuf + g * 15 * n3p;
+  {
+    const real Wv = sW[v * n3p + pn];
+#pragma unroll
+    for (int l = 0; l < 3; ++l) myb[(l * NV + v) * n3p + pn] = col[l] * Wv;
+  }
+  cluster_barrier();  // both halves' lifting fields staged
+  {
+    const real* peer = cluster_peer(sbuf, r ^ 1u);
+    for (int it = tid; it < 3 * NV * h3; it += T) {
+      const int gg = it / (NV * h3), rem = it - gg * NV * h3;
+      const int c = rem / h3, m = rem - c * h3;
+      const int o = (gg * 15 + 2 * NV + c) * n3p + pidx<n>(m % n, (m / n) % n, kb + m / n2);
+      sbuf[o] = peer[o];
+    }
+  }
+  __syncthreads();
+  // dW_v/dx_g: the three reference-direction sweeps of node_sweep3, then the face terms
+  real acc = real(0);
+#pragma unroll
+  for (int a = 0; a < n; ++a) {
+    const real d0 = sOp[a * n + i], d1 = sOp[a * n + j], d2 = sOp[a * n + k];
+    acc += d0 * myb[v * n3p + pidx<n>(a, j, k)];
+    acc += d1 * myb[(NV + v) * n3p + pidx<n>(i, a, k)];
+    acc += d2 * myb[(2 * NV + v) * n3p + pidx<n>(i, j, a)];
+  }
+  {
+    const real* lhm = sOp + n2 + 2 * n;
+    const real* lhp = sOp + n2 + 3 * n;
+    const int pq0 = j + n * k, pq1 = i + n * k, pq2 = i + n * j;
+    const int o = (v * 3 + g) * n2;
+    if constexpr (LGL) {
+      if (i == 0) acc = dg_fma(lhm[0], sQ[0 * 15 * n2 + o + pq0], acc);
+      if (i == n - 1) acc = dg_fma(lhp[n - 1], sQ[1 * 15 * n2 + o + pq0], acc);
+      if (j == 0) acc = dg_fma(lhm[0], sQ[2 * 15 * n2 + o + pq1], acc);
+      if (j == n - 1) acc = dg_fma(lhp[n - 1], sQ[3 * 15 * n2 + o + pq1], acc);
+      if (k == 0) acc = dg_fma(lhm[0], sQ[4 * 15 * n2 + o + pq2], acc);
+      if (k == n - 1) acc = dg_fma(lhp[n - 1], sQ[5 * 15 * n2 + o + pq2], acc);
+    } else {
+      acc = dg_fma(lhm[i], sQ[0 * 15 * n2 + o + pq0], acc);
+      acc = dg_fma(lhp[i], sQ[1 * 15 * n2 + o + pq0], acc);
+      acc = dg_fma(lhm[j], sQ[2 * 15 * n2 + o + pq1], acc);
+      acc = dg_fma(lhp[j], sQ[3 * 15 * n2 + o + pq1], acc);
+      acc = dg_fma(lhm[k], sQ[4 * 15 * n2 + o + pq2], acc);
+      acc = dg_fma(lhp[k], sQ[5 * 15 * n2 + o + pq2], acc);
+    }
+  }
+  __syncthreads();  // surface terms read: the buffer takes the gradients
+  real* sG = sQ;    // [15][n3p], component d*5 + v
+  const real grad = acc * sj;
+  sG[(g * NV + v) * n3p + pn] = grad;
+  if (Gvol != nullptr) Gvol[((size_t)e * 15 + g * NV + v) * n3 + node] = grad;
+  cluster_barrier();  // both halves' gradients; the other CTA has copied its lifting fields
+  if constexpr (!LGL) {  // Gauss: the k faces interpolate whole lines along k
+    const real* peer = cluster_peer(sG, r ^ 1u);
+    for (int it = tid; it < 15 * h3; it += T) {
+      const int c = it / h3, m = it - c * h3;
+      const int o = c * n3p + pidx<n>(m % n, (m / n) % n, kb + m / n2);
+      sG[o] = peer[o];
+    }
+    __syncthreads();
+  }
+  // a4: this half's face nodes, one thread per (face node, component): faces 0-3 with
+  // q in [r n/2, (r + 1) n/2), then face 4 + r whole
+  constexpr int nIJ = 4 * 15 * n2 / 2;
+  for (int it = tid; it < nIJ + 15 * n2; it += T) {
+    int s, c, p, q;
+    if (it < nIJ) {
+      s = it / (15 * n2 / 2);
+      const int rem = it - s * (15 * n2 / 2);
+      c = rem / (n2 / 2);
+      const int m = rem - c * (n2 / 2);
+      p = m % n;
+      q = (int)r * hk + m / n;
+    } else {
+      s = 4 + (int)r;
+      const int rem = it - nIJ;
+      c = rem / n2;
+      const int pq = rem - c * n2;
+      p = pq % n;
+      q = pq / n;
+    }
+    const int l = s >> 1, pq = p + n * q;
+    const real* b = sG + c * n3p;
+    real val = real(0);
+    if (LGL) {
+      val = b[pvol_index<n>(l, (s & 1) ? n - 1 : 0, p, q)];
+    } else {
+#pragma unroll
+      for (int a = 0; a < n; ++a) val = dg_fma((s & 1) ? ops.lp[a] : ops.lm[a], b[pvol_index<n>(l, a, p, q)], val);
+    }
+    Gf[((size_t)sSlot[s] * 15 + c) * n2 + sMpq[s * n2 + pq]] = val;
+  }
+  // a6: flux component (F_d)_v, d = g, with the expressions of flux_total
+  real F;
+  {
+    real Wn[NV];
+#pragma unroll
+    for (int c = 0; c < NV; ++c) Wn[c] = sW[c * n3p + pn];
+    const int d = g;
+    const real* Gn = sG + pn;
+    const real ud = d == 0 ? Wn[1] : (d == 1 ? Wn[2] : Wn[3]);
+    const real p = Wn[4];
+    if (v == 0) {
+      F = d == 0 ? Uo[1] : (d == 1 ? Uo[2] : Uo[3]);
+    } else {
+      const real div = Gn[(0 * 5 + 1) * n3p] + Gn[(1 * 5 + 2) * n3p] + Gn[(2 * 5 + 3) * n3p];
+      if (v < 4) {
+        const int c = v - 1;
+        real tau = ph.mu * (Gn[(d * 5 + 1 + c) * n3p] + Gn[(c * 5 + 1 + d) * n3p]);
+        if (c == d) tau -= real(2.0 / 3.0) * ph.mu * div;
+        const real Uc = v == 1 ? Uo[1] : (v == 2 ? Uo[2] : Uo[3]);
+        F = Uc * ud - tau;
+        if (c == d) F += p;
+      } else {
+        real tau[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          tau[c] = ph.mu * (Gn[(d * 5 + 1 + c) * n3p] + Gn[(c * 5 + 1 + d) * n3p]);
+          if (c == d) tau[c] -= real(2.0 / 3.0) * ph.mu * div;
+        }
+        const real ir = real(1) / Wn[0];
+        const real dT = (Gn[(d * 5 + 4) * n3p] - p * ir * Gn[(d * 5 + 0) * n3p]) * ir;
+        const real fv4 = tau[0] * Wn[1] + tau[1] * Wn[2] + tau[2] * Wn[3] + ph.lam_th * dT;
+        F = ud * (Uo[4] + p) - fv4;
+      }
+    }
+  }
+  real* sF = sbuf + 15 * n3p;
+  real* sC = sbuf + 2 * 15 * n3p;
+  sF[(g * NV + v) * n3p + pn] = F;
+  __syncthreads();
+  // contravariant flux of reference direction g, variable v
+  sC[(g * NV + v) * n3p + pn] = dg_fma(row[2], sF[(2 * NV + v) * n3p + pn],
+                                       dg_fma(row[1], sF[(NV + v) * n3p + pn], row[0] * sF[v * n3p + pn]));
+  cluster_barrier();  // both halves' contravariant fluxes; the other CTA is done with the gradients
+  {
+    const real* peer = cluster_peer(sC, r ^ 1u);
+    for (int it = tid; it < NV * h3; it += T) {
+      const int c = it / h3, m = it - c * h3;
+      const int o = (2 * NV + c) * n3p + pidx<n>(m % n, (m / n) % n, kb + m / n2);
+      sC[o] = peer[o];
+    }
+  }
+  cluster_arrive();  // this CTA's reads of the other one are done (waited for before exit)
+  __syncthreads();
+  // a7: D_hat sweep of the contravariant flux along direction g
+  const int il = g == 0 ? i : (g == 1 ? j : k);
+  real sum = real(0);
+#pragma unroll
+  for (int a = 0; a < n; ++a) {
+    const real dh = sOp[a * n + il];
+    const int ia = g == 0 ? pidx<n>(a, j, k) : (g == 1 ? pidx<n>(i, a, k) : pidx<n>(i, j, a));
+    sum = dg_fma(dh, sC[(g * NV + v) * n3p + ia], sum);
+  }
+  sF[(g * NV + v) * n3p + pn] = sum;  // region 1: read by no one since the last cluster barrier
+  __syncthreads();
+  if (g == 0)
+    Utv[((size_t)e * NV + v) * n3 + node] = sF[v * n3p + pn] + sF[(NV + v) * n3p + pn] + sF[(2 * NV + v) * n3p + pn];
+  cluster_wait();  // the other CTA has finished reading this one's shared memory
+}
+
 template <typename real, int n, int SW, bool LGL, int SPLIT, bool BR2>
 constexpr auto lift_vol_kernel() {
   if constexpr (lift_vol_min_blocks<real, n, SW, SPLIT, BR2>() > 0)
@@ -1154,14 +1444,17 @@ __global__ void __launch_bounds__(128, sizeof(real) == 4 ? 8 : 1) k_face(const r
 
 // The same flux for small meshes (few face nodes per SM): 32 face nodes per CTA of three
 // warps, warp 0 computing the Riemann flux, warps 1 and 2 the viscous normal fluxes of
-// the two sides, combined through shared memory.  Each thread runs a third of the
-// dependent FP64 chain of k_face, which is what bounds a mesh that leaves most SMs idle.
+// the two sides, combined through shared memory; for the Roe fluxes a fourth warp takes
+// the central part F(W_L).n + F(W_R).n and warp 0 the dissipation only.  Each thread runs
+// a part of the dependent FP64 chain of k_face (an FP64 warp instruction holds its SM
+// sub-partition for 64 clocks), which is what bounds a mesh that leaves most SMs idle.
 template <typename real, int n, int RS>
-__global__ void __launch_bounds__(96) k_face3(const real* __restrict__ Wf, const real* __restrict__ Gf,
-                                              const real* __restrict__ fgeo, real* __restrict__ Ff, int S,
-                                              int nSface, int nBC, Phys<real> ph) {
+__global__ void __launch_bounds__(128) k_face3(const real* __restrict__ Wf, const real* __restrict__ Gf,
+                                               const real* __restrict__ fgeo, real* __restrict__ Ff, int S,
+                                               int nSface, int nBC, Phys<real> ph) {
   constexpr int n2 = n * n;
-  __shared__ real sf[3][NV][32];
+  constexpr int R = RS == 0 ? 4 : 3;  // warps: Riemann (dissipation), viscous master, viscous slave, (central)
+  __shared__ real sf[R][NV][32];
   const int role = threadIdx.x >> 5, lane = threadIdx.x & 31;  // warp-uniform role
   const int idx = blockIdx.x * 32 + lane;
   const bool live = idx < nSface * n2;
@@ -1171,14 +1464,21 @@ __global__ void __launch_bounds__(96) k_face3(const real* __restrict__ Wf, const
   for (int d = 0; d < 3; ++d) nv[d] = fgeo[((size_t)side * 4 + d) * n2 + pq];
   const bool bnd = side < nBC;
   real out[NV];
-  if (role == 0) {
+  if (role == 0 || role == 3) {
     real WL[NV], WR[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       WL[v] = Wf[((size_t)side * NV + v) * n2 + pq];
       WR[v] = Wf[((size_t)(S + side) * NV + v) * n2 + pq];
     }
-    riemann_kind<RS>(WL, WR, real(1) / WL[0], real(1) / WR[0], nv, ph, out);
+    if constexpr (RS == 0) {
+      if (role == 0)
+        roe_dissipation(WL, WR, real(1) / WL[0], real(1) / WR[0], nv, ph, ph.riemann == 2, out);
+      else
+        roe_central(WL, WR, nv, ph, out);
+    } else {
+      riemann_kind<RS>(WL, WR, real(1) / WL[0], real(1) / WR[0], nv, ph, out);
+    }
   } else {
     // role 1: the master (slot 0) side, role 2: the slave or boundary (slot 1) side,
     // whose gradients on a boundary are the inner ones
@@ -1197,8 +1497,10 @@ __global__ void __launch_bounds__(96) k_face3(const real* __restrict__ Wf, const
   if (role == 0 && live) {
     const real sa = fgeo[((size_t)side * 4 + 3) * n2 + pq];
 #pragma unroll
-    for (int v = 0; v < NV; ++v)
-      Ff[((size_t)side * NV + v) * n2 + pq] = (sf[0][v][lane] - real(0.5) * (sf[1][v][lane] + sf[2][v][lane])) * sa;
+    for (int v = 0; v < NV; ++v) {
+      const real f = RS == 0 ? real(0.5) * (sf[R - 1][v][lane] - sf[0][v][lane]) : sf[0][v][lane];  // riemann_roe's (S - D) / 2
+      Ff[((size_t)side * NV + v) * n2 + pq] = (f - real(0.5) * (sf[1][v][lane] + sf[2][v][lane])) * sa;
+    }
   }
 }
 
@@ -1335,6 +1637,308 @@ __global__ void __launch_bounds__(Cfg<n>::T * TM, TM > 1 ? 1 : ((sizeof(real) ==
   }
 }
 
+// a5 and a8-a10 in one kernel for small FP64 meshes (n = 4, fewer elements than SMs, BR1,
+// no mortars): each element computes the numerical fluxes of its six sides itself (an inner
+// side twice, once by each of its elements), one thread per (warp role of k_face3, face
+// node) with k_face3's arithmetic in the master frame of each side, so the fluxes are the
+// same values; then the surface integral, -1/J and the RK update with one thread per
+// (variable, node) and k_surf's expressions, and the face states of the new U.  On such
+// meshes each kernel's chain of dependent instructions, not its work, sets the time, and
+// this removes one kernel per stage.  The face states are read from WfIn and the new ones
+// written to WfOut, another buffer: a neighbouring element may still read the old states
+// of a shared side.
+template <int RS, bool LGL>
+__global__ void __launch_bounds__(384) k_surf_face(
+    const double* __restrict__ WfIn, const double* __restrict__ Gf, const double* __restrict__ fgeo,
+    const int* __restrict__ elemSide, const double* __restrict__ sJ, const double* __restrict__ Utv,
+    double* __restrict__ U, double* __restrict__ dU, double* __restrict__ WfOut, const double* __restrict__ xsol,
+    RkStage<double> rk, double t, SourceParams src, int K, int S, int nBC, Ops<double> ops, Phys<double> ph,
+    unsigned* __restrict__ status) {
+  using real = double;
+  constexpr int n = 4, n2 = n * n, n3 = n2 * n, n3p = Cfg<n>::n3p, T = 384, FN = 6 * n2;
+  constexpr int R = RS == 0 ? 4 : 3;  // roles of k_face3
+  static_assert(R * FN <= T && NV * n3 <= T, "one thread per (role, face node) and per (variable, node)");
+  __shared__ real sf[R][NV][FN];
+  __shared__ real sSa[FN];          // s_hat of the face nodes (read with the normals)
+  __shared__ real sF[6 * NV * n2];  // [6][5][n2] f* s_hat with the element's sign (k_surf's layout)
+  __shared__ real sU[NV * n3p];
+  __shared__ real sOp[n2 + 4 * n];
+  __shared__ int sES[6];
+  const int tid = threadIdx.x;
+  const int e = blockIdx.x;  // grid = K
+  // the (variable, node) of the update, whose global values are requested first
+  const bool upd = tid < NV * n3;
+  const int uv = upd ? tid / n3 : 0;  // warp-uniform
+  const int node = upd ? tid - uv * n3 : 0;
+  const int i = node % n, j = (node / n) % n, k = node / n2;
+  const size_t gidx = ((size_t)e * NV + uv) * n3 + node;
+  real vtv = real(0), vU = real(0), vdU = real(0), sj = real(0);
+  if (upd) {
+    vtv = Utv[gidx];
+    vU = U[gidx];
+    vdU = dU[gidx];
+    sj = sJ[(size_t)e * n3 + node];
+  }
+  load_ops<real, n>(sOp, ops, tid, T);
+  if (tid < 6) sES[tid] = elemSide[(size_t)e * 6 + tid];
+  __syncthreads();
+  // a5: role (warp-uniform: FN is a multiple of 32) and face node of the element
+  const int role = tid / FN, fn = tid - role * FN;
+  if (role < R) {
+    const int s = fn / n2, pq = fn - s * n2;
+    const int es = sES[s];
+    const int side = es_side(es);
+    const int mpq = orient_pq(es_orient(es), n - 1, pq % n, pq / n);
+    real nv[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) nv[d] = fgeo[((size_t)side * 4 + d) * n2 + mpq];
+    if (role == 0) sSa[fn] = fgeo[((size_t)side * 4 + 3) * n2 + mpq];
+    const bool bnd = side < nBC;
+    real out[NV];
+    if (role == 0 || role == 3) {
+      real WL[NV], WR[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        WL[v] = WfIn[((size_t)side * NV + v) * n2 + mpq];
+        WR[v] = WfIn[((size_t)(S + side) * NV + v) * n2 + mpq];
+      }
+      if constexpr (RS == 0) {
+        if (role == 0)
+          roe_dissipation(WL, WR, real(1) / WL[0], real(1) / WR[0], nv, ph, ph.riemann == 2, out);
+        else
+          roe_central(WL, WR, nv, ph, out);
+      } else {
+        riemann_kind<RS>(WL, WR, real(1) / WL[0], real(1) / WR[0], nv, ph, out);
+      }
+    } else {
+      const int slot = role - 1;  // master, slave or boundary side (inner gradients on a boundary)
+      real Wx[NV], Gx[15];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) Wx[v] = WfIn[((size_t)(slot * S + side) * NV + v) * n2 + mpq];
+      const int gslot = bnd ? 0 : slot;
+#pragma unroll
+      for (int c = 0; c < 15; ++c) Gx[c] = Gf[((size_t)(gslot * S + side) * 15 + c) * n2 + mpq];
+      visc_normal(Wx, real(1) / Wx[0], Gx, nv, ph, out);
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) sf[role][v][fn] = out[v];
+  }
+  __syncthreads();
+  if (tid < FN) {  // k_face3's combination times s_hat, then the element's sign (k_surf's gather)
+    const int s = tid / n2, pq = tid - s * n2;
+    const real sa = sSa[tid];
+    const bool slave = es_slave(sES[s]);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const real f = RS == 0 ? real(0.5) * (sf[R - 1][v][tid] - sf[0][v][tid]) : sf[0][v][tid];
+      sF[(s * NV + v) * n2 + pq] = dg_neg_if((f - real(0.5) * (sf[1][v][tid] + sf[2][v][tid])) * sa, slave);
+    }
+  }
+  __syncthreads();
+  // a8-a10 for variable uv at the node, with k_surf's expressions (dt folded into -1/J)
+  if (upd) {
+    const real* lhm = sOp + n2 + 2 * n;
+    const real* lhp = sOp + n2 + 3 * n;
+    const int pq0 = j + n * k, pq1 = i + n * k, pq2 = i + n * j;
+    real a = vtv;
+    if (LGL) {
+      if (i == 0) a = dg_fma(lhm[i], sF[(0 * NV + uv) * n2 + pq0], a);
+      if (i == n - 1) a = dg_fma(lhp[i], sF[(1 * NV + uv) * n2 + pq0], a);
+      if (j == 0) a = dg_fma(lhm[j], sF[(2 * NV + uv) * n2 + pq1], a);
+      if (j == n - 1) a = dg_fma(lhp[j], sF[(3 * NV + uv) * n2 + pq1], a);
+      if (k == 0) a = dg_fma(lhm[k], sF[(4 * NV + uv) * n2 + pq2], a);
+      if (k == n - 1) a = dg_fma(lhp[k], sF[(5 * NV + uv) * n2 + pq2], a);
+    } else {
+      a = dg_fma(lhm[i], sF[(0 * NV + uv) * n2 + pq0], a);
+      a = dg_fma(lhp[i], sF[(1 * NV + uv) * n2 + pq0], a);
+      a = dg_fma(lhm[j], sF[(2 * NV + uv) * n2 + pq1], a);
+      a = dg_fma(lhp[j], sF[(3 * NV + uv) * n2 + pq1], a);
+      a = dg_fma(lhm[k], sF[(4 * NV + uv) * n2 + pq2], a);
+      a = dg_fma(lhp[k], sF[(5 * NV + uv) * n2 + pq2], a);
+    }
+    real ut = a * -(rk.dt * sj);
+    if (src.on) {
+      double x[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) x[c] = xsol[((size_t)e * 3 + c) * n3 + node];
+      double Sv[NV];
+      manufactured_source(x, t, src.gamma, src.mu, src.Pr, Sv);
+      const double Su = uv == 0 ? Sv[0] : (uv == 1 ? Sv[1] : (uv == 2 ? Sv[2] : (uv == 3 ? Sv[3] : Sv[4])));
+      ut = dg_fma(rk.dt, (real)Su, ut);
+    }
+    const real du = dg_fma(rk.A, vdU, ut);  // A dU + dt U_t
+    const real un = dg_fma(rk.B, du, vU);
+    dU[gidx] = du;
+    U[gidx] = un;
+    sU[uv * n3p + pidx<n>(i, j, k)] = un;
+  }
+  if (rk.prolong) {
+    __syncthreads();
+    faces_from_volume<real, n, LGL>(sU, ops, sES, e, K, S, WfOut, ph, status, tid, T);
+  }
+}
+
+// k_surf_face on Gauss-Lobatto nodes with two CTAs per element (meshes with at most half as
+// many elements as SMs): CTA r takes the nodes with k in [r n/2, (r + 1) n/2) and the face
+// nodes that they lie on (faces 0-3 with q in that range, face 4 + r).  On Gauss-Lobatto
+// nodes a node receives the flux and gives the state of a face only where it lies on it,
+// so the two halves share nothing.  Warps are role-uniform, two per role over the half's
+// 48 face nodes, ordered so that each SM sub-partition gets the Riemann dissipation and the
+// central flux, or the two viscous fluxes (FP64 warp instructions, which hold a
+// sub-partition for 64 clocks whatever their active lanes, set the time here).  Fluxes,
+// update and face states use the expressions of k_surf_face.
+template <int RS>
+__global__ void __launch_bounds__(256) k_surf_face2(
+    const double* __restrict__ WfIn, const double* __restrict__ Gf, const double* __restrict__ fgeo,
+    const int* __restrict__ elemSide, const double* __restrict__ sJ, const double* __restrict__ Utv,
+    double* __restrict__ U, double* __restrict__ dU, double* __restrict__ WfOut, const double* __restrict__ xsol,
+    RkStage<double> rk, double t, SourceParams src, int K, int S, int nBC, Ops<double> ops, Phys<double> ph,
+    unsigned* __restrict__ status) {
+  using real = double;
+  constexpr int n = 4, n2 = n * n, n3 = n2 * n, n3p = Cfg<n>::n3p, hk = n / 2, h3 = n3 / 2;
+  constexpr int R = RS == 0 ? 4 : 3, T = 2 * 32 * R;
+  constexpr int FIJ = 4 * (n2 / 2), FH = FIJ + n2;  // face nodes of a half: faces 0-3, then face 4 + r
+  static_assert(FH <= 64 && NV * h3 <= T, "two warps per role, one thread per (variable, node)");
+  __shared__ real sf[R][NV][FH];
+  __shared__ real sSa[FH];          // s_hat of the half's face nodes (read with the normals)
+  __shared__ real sF[6 * NV * n2];  // k_surf's layout; only this half's face nodes are filled
+  __shared__ real sU[NV * n3p];     // only this half's nodes are filled
+  __shared__ real sOp[n2 + 4 * n];
+  __shared__ int sES[6];
+  const int tid = threadIdx.x;
+  const int e = blockIdx.x >> 1, r = blockIdx.x & 1;  // grid = 2 K
+  // half face node fh -> (side s of the element, face node pq)
+  auto face_node = [r](int fh, int& s, int& pq) {
+    if (fh < FIJ) {
+      s = fh / (n2 / 2);
+      const int m = fh - s * (n2 / 2);
+      pq = m % n + n * (r * hk + m / n);
+    } else {
+      s = 4 + r;
+      pq = fh - FIJ;
+    }
+  };
+  const bool upd = tid < NV * h3;
+  const int uv = upd ? tid / h3 : 0;  // warp-uniform
+  const int ln = tid & 31;
+  const int i = ln % n, j = (ln / n) % n, k = r * hk + ln / n2;
+  const int node = i + n * (j + n * k);
+  const size_t gidx = ((size_t)e * NV + uv) * n3 + node;
+  real vtv = real(0), vU = real(0), vdU = real(0), sj = real(0);
+  if (upd) {
+    vtv = Utv[gidx];
+    vU = U[gidx];
+    vdU = dU[gidx];
+    sj = sJ[(size_t)e * n3 + node];
+  }
+  load_ops<real, n>(sOp, ops, tid, T);
+  if (tid < 6) sES[tid] = elemSide[(size_t)e * 6 + tid];
+  __syncthreads();
+  // a5: warp w takes role {0, 0, 1, 1, 3, 3, 2, 2}[w] (Roe) or {0, 0, 1, 1, 2, 2}[w]
+  const int w = tid >> 5;
+  const int role = w < 2 ? 0 : (w < 4 ? 1 : (RS == 0 ? (w < 6 ? 3 : 2) : 2));
+  const int fh = (w & 1) * 32 + ln;
+  if (fh < FH) {
+    int s, pq;
+    face_node(fh, s, pq);
+    const int es = sES[s];
+    const int side = es_side(es);
+    const int mpq = orient_pq(es_orient(es), n - 1, pq % n, pq / n);
+    real nv[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) nv[d] = fgeo[((size_t)side * 4 + d) * n2 + mpq];
+    if (role == 0) sSa[fh] = fgeo[((size_t)side * 4 + 3) * n2 + mpq];
+    const bool bnd = side < nBC;
+    real out[NV];
+    if (role == 0 || role == 3) {
+      real WL[NV], WR[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        WL[v] = WfIn[((size_t)side * NV + v) * n2 + mpq];
+        WR[v] = WfIn[((size_t)(S + side) * NV + v) * n2 + mpq];
+      }
+      if constexpr (RS == 0) {
+        if (role == 0)
+          roe_dissipation(WL, WR, real(1) / WL[0], real(1) / WR[0], nv, ph, ph.riemann == 2, out);
+        else
+          roe_central(WL, WR, nv, ph, out);
+      } else {
+        riemann_kind<RS>(WL, WR, real(1) / WL[0], real(1) / WR[0], nv, ph, out);
+      }
+    } else {
+      const int slot = role - 1;
+      real Wx[NV], Gx[15];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) Wx[v] = WfIn[((size_t)(slot * S + side) * NV + v) * n2 + mpq];
+      const int gslot = bnd ? 0 : slot;
+#pragma unroll
+      for (int c = 0; c < 15; ++c) Gx[c] = Gf[((size_t)(gslot * S + side) * 15 + c) * n2 + mpq];
+      visc_normal(Wx, real(1) / Wx[0], Gx, nv, ph, out);
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) sf[role][v][fh] = out[v];
+  }
+  __syncthreads();
+  if (tid < FH) {
+    int s, pq;
+    face_node(tid, s, pq);
+    const real sa = sSa[tid];
+    const bool slave = es_slave(sES[s]);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const real f = RS == 0 ? real(0.5) * (sf[R - 1][v][tid] - sf[0][v][tid]) : sf[0][v][tid];
+      sF[(s * NV + v) * n2 + pq] = dg_neg_if((f - real(0.5) * (sf[1][v][tid] + sf[2][v][tid])) * sa, slave);
+    }
+  }
+  __syncthreads();
+  if (upd) {
+    const real* lhm = sOp + n2 + 2 * n;
+    const real* lhp = sOp + n2 + 3 * n;
+    const int pq0 = j + n * k, pq1 = i + n * k, pq2 = i + n * j;
+    real a = vtv;
+    if (i == 0) a = dg_fma(lhm[i], sF[(0 * NV + uv) * n2 + pq0], a);
+    if (i == n - 1) a = dg_fma(lhp[i], sF[(1 * NV + uv) * n2 + pq0], a);
+    if (j == 0) a = dg_fma(lhm[j], sF[(2 * NV + uv) * n2 + pq1], a);
+    if (j == n - 1) a = dg_fma(lhp[j], sF[(3 * NV + uv) * n2 + pq1], a);
+    if (k == 0) a = dg_fma(lhm[k], sF[(4 * NV + uv) * n2 + pq2], a);
+    if (k == n - 1) a = dg_fma(lhp[k], sF[(5 * NV + uv) * n2 + pq2], a);
+    real ut = a * -(rk.dt * sj);
+    if (src.on) {
+      double x[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) x[c] = xsol[((size_t)e * 3 + c) * n3 + node];
+      double Sv[NV];
+      manufactured_source(x, t, src.gamma, src.mu, src.Pr, Sv);
+      const double Su = uv == 0 ? Sv[0] : (uv == 1 ? Sv[1] : (uv == 2 ? Sv[2] : (uv == 3 ? Sv[3] : Sv[4])));
+      ut = dg_fma(rk.dt, (real)Su, ut);
+    }
+    const real du = dg_fma(rk.A, vdU, ut);
+    const real un = dg_fma(rk.B, du, vU);
+    dU[gidx] = du;
+    U[gidx] = un;
+    sU[uv * n3p + pidx<n>(i, j, k)] = un;
+  }
+  if (rk.prolong) {
+    __syncthreads();
+    if (tid < FH) {  // faces_from_volume's Gauss-Lobatto copy for this half's face nodes
+      int s, pq;
+      face_node(tid, s, pq);
+      const int l = s >> 1, p = pq % n, q = pq / n;
+      const int vi = pvol_index<n>(l, (s & 1) ? n - 1 : 0, p, q);
+      real Uf[NV], W[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) Uf[v] = sU[v * n3p + vi];
+      cons_to_prim(Uf, W, ph);
+      if (!(W[0] > real(0)) || !(W[4] > real(0))) atomicOr(status, 1u);
+      const int es = sES[s];
+      const int mpq = orient_pq(es_orient(es), n - 1, p, q);
+      real* dst = WfOut + ((size_t)(es_slave(es) * S + es_side(es)) * NV) * n2 + mpq;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) dst[v * n2] = W[v];
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
@@ -1408,6 +2012,15 @@ cudaError_t launch_lift_vol(const DevMesh& m, const real* U, const Ops<real>& op
     }
   }
   if constexpr (sizeof(real) == 8) {
+    // at most half as many elements as SMs at n = 4: two CTAs per element (k_lift_vol_c2)
+    if (!m.br2 && m.split == 0 && m.n == 4 && 2 * m.K <= m.nsm) {
+      auto* kc2 = m.lgl ? &k_lift_vol_c2<4, true> : &k_lift_vol_c2<4, false>;
+      kc2<<<2 * m.K, 15 * 64 / 2, 0, st>>>(U, (const double*)m.Ja, (const double*)m.sJ, (const double*)m.Wf,
+                                          (const double*)m.fgeo, m.elemSide, (double*)m.Gf, (double*)m.Utv,
+                                          store_grad ? (double*)m.Gvol : nullptr, m.K, m.S, m.Sface,
+                                          (const double*)m.QB, ops, ph);
+      return cudaGetLastError();
+    }
     // fewer elements than SMs at n <= 4: three thread groups per element (k_lift_vol_g3)
     if (!m.br2 && m.split == 0 && m.n <= 4 && m.K < m.nsm) {
 #define FLEXI_G3(NN, LG)                                                                                   \
@@ -1455,7 +2068,7 @@ cudaError_t launch_face(const DevMesh& m, const Phys<real>& ph, cudaStream_t st)
   if ((tot + 127) / 128 < 2 * m.nsm) {
     const int grid = (tot + 31) / 32;
 #define FLEXI_FACE3(RSV)                                                                                    \
-  FLEXI_DISPATCH_N(m.n, (k_face3<real, NN, RSV><<<grid, 96, 0, st>>>((const real*)m.Wf, (const real*)m.Gf, \
+  FLEXI_DISPATCH_N(m.n, (k_face3<real, NN, RSV><<<grid, RSV == 0 ? 128 : 96, 0, st>>>((const real*)m.Wf, (const real*)m.Gf, \
                                                                     (const real*)m.fgeo, (real*)m.Ff, m.S, \
                                                                     m.Sface, m.nBC, ph)))
     switch (ph.riemann) {

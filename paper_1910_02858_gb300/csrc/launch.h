@@ -88,6 +88,13 @@ template <typename real>
 cudaError_t launch_surf(const DevMesh& m, int mode, real* U, real* dU, real* Ut, const RkStage<real>& rk,
                         double t, const SourceParams& src, const Ops<real>& ops, const Phys<real>& ph,
                         cudaStream_t st);
+
+// a5 and a8-a10 of an RK stage in one kernel (FP64, n = 4, no mortars, BR1; meant for
+// meshes with fewer elements than SMs): face states read from WfIn, those of the new U
+// written to WfOut when rk.prolong (WfOut != WfIn: other elements still read WfIn)
+cudaError_t launch_surf_face(const DevMesh& m, const void* WfIn, void* WfOut, double* U, double* dU,
+                             const RkStage<double>& rk, double t, const SourceParams& src, const Ops<double>& ops,
+                             const Phys<double>& ph, cudaStream_t st);
 // adjoint of the right-hand side: out = (dL/dU)^T lam  (uses Gvol written by
 // launch_lift_vol with store_grad = 1); mode 1 accumulates out += scale * result
 template <typename real>

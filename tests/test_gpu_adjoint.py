@@ -107,7 +107,8 @@ def test_c5_gradient_fd_and_oracle(c5):
     # J = sum w J |m|^2 / (2 rho): its gradient with respect to U_T by the same reduction
     wJ = torch.tensor(_oracle(sk, mesh).quad_weights().numpy(), device=DEV).unsqueeze(1)
     J = (wJ[:, 0] * 0.5 * (UT[:, 1] ** 2 + UT[:, 2] ** 2 + UT[:, 3] ** 2) / UT[:, 0]).sum()
-    assert abs(float(J) - _ke(s, UT.detach())) < 1e-12 * float(J)
+    Jv = J.item()
+    assert abs(Jv - _ke(s, UT.detach())) < 1e-12 * Jv
     J.backward()
     grad = U0d.grad.detach()
     # central finite differences (eps = 1e-6) in 16 seeded directions with unit

@@ -6,6 +6,10 @@
   neighbour along that direction, its other faces are ordinary sides.
 - Small N with several elements per CTA (N = 1: 8 elements, N = 2: 3 elements per
   CTA) and an element count that leaves the last CTA partly empty.
+- The small-mesh lifting/volume kernels at n = 4 (FP64): a cluster of two CTAs per
+  element when there are at most half as many elements as SMs (48 elements, Gauss and
+  Gauss-Lobatto, reoriented sides), three thread groups in one CTA per element below
+  one element per SM (100 elements).
 - Zero steps: flexi_rk_run and flexi_rk_run_host leave the state unchanged.
 
 Right-hand sides use the rounding-sensitivity tolerance of test_gpu_parity, states
@@ -28,6 +32,9 @@ CASES = [
     ("one_thick_lg_N4_hllc", dict(nelem=(1, 2, 3), reorient_seed=5), dict(N=4, riemann=1)),
     ("ragged_cta_lg_N1_roe", dict(nelem=(3, 1, 3), reorient_seed=3), dict(N=1, riemann=0)),  # 9 elements, 8 per CTA
     ("ragged_cta_lg_N2_hllc", dict(nelem=(2, 2, 2), reorient_seed=4), dict(N=2, riemann=1)),  # 8 elements, 3 per CTA
+    ("cluster_pair_lg_N3_hllc", dict(nelem=(4, 4, 3), reorient_seed=6), dict(N=3, riemann=1)),
+    ("cluster_pair_lgl_N3_roe", dict(nelem=(3, 4, 4), reorient_seed=8), dict(N=3, node_type=1, riemann=0)),
+    ("three_groups_lg_N3_hllc", dict(nelem=(5, 5, 4), reorient_seed=7), dict(N=3, riemann=1)),
 ]
 
 

@@ -236,6 +236,9 @@ def test_reduce_matches_oracle():
 
 
 def test_run_host_matches_device_path():
+    """flexi_rk_run_host, flexi_rk_run (graph replay) and separate flexi_rk_step calls
+    give the same bits (the first two hand the face states from step to step through
+    the last stage, the third prolongs U at every step)."""
     mesh = wl.box_mesh((3, 3, 3), Ngeo=1)
     sk = dict(N=3, riemann=1)
     s = _solver(sk, mesh)
@@ -246,8 +249,11 @@ def test_run_host_matches_device_path():
     F.flexi_rk_run_host(s.ctx, Uh, 3, 0.0, 1e-3, torch.cuda.current_stream())
     Ud = U0.to(DEV)
     s.run(Ud, 3, 1e-3)
+    Ue = U0.to(DEV)
+    s.run(Ue, 3, 1e-3, graph=False)
     torch.cuda.synchronize()
     assert torch.equal(Uh, Ud.cpu())
+    assert torch.equal(Ud, Ue)
     s.close()
 
 
@@ -294,7 +300,11 @@ def test_kernel_timing_hooks():
     F.flexi_profile(s.ctx, True)
     s.run(U, 2, 1e-3)
     t = F.flexi_kernel_times(s.ctx)
-    assert t["lift_vol"][1] == 10 and t["face"][1] == 10 and t["surf_rk"][1] == 10 and t["prolong"][1] == 2
+    # one prolongation: the second step takes its face states from the first step's last stage;
+    # with fewer elements than SMs (FP64, n = 4, BR1) k_surf_face computes the face fluxes
+    fused = mesh.K < torch.cuda.get_device_properties(0).multi_processor_count
+    assert t["lift_vol"][1] == 10 and t["surf_rk"][1] == 10 and t["prolong"][1] == 1
+    assert t["face"][1] == (0 if fused else 10)
     assert all(v[0] >= 0 for v in t.values())
     s.close()
 
