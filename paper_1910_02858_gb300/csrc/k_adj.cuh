@@ -106,13 +106,13 @@ __device__ __forceinline__ void conv_vjp(const real U[NV], const real W[NV], int
 }
 
 template <typename real>
-__device__ __forceinline__ void absf_vjp(real x, real del, bool smooth, real& val, real& dx, real& ddel) {
+__device__ __forceinline__ void absf_vjp(real x, real del, real idel, bool smooth, real& val, real& dx, real& ddel) {
   const real ax = dg_abs(x);
-  if (smooth && ax < del) {
-    const real ih = real(0.5) / del;
+  if (smooth && ax < del) {  // idel = 1 / del
+    const real ih = real(0.5) * idel;
     val = (x * x + del * del) * ih;
-    dx = x / del;
-    ddel = (del * del - x * x) * ih / del;
+    dx = x * idel;
+    ddel = (del * del - x * x) * ih * idel;
   } else {
     val = ax;
     dx = x < real(0) ? real(-1) : (x > real(0) ? real(1) : real(0));
@@ -132,17 +132,22 @@ __device__ __forceinline__ void roe_vjp(const real WL[NV], const real WR[NV], co
   const real ER = WR[4] * ph.inv_gm1 + real(0.5) * WR[0] * q2R;
   const real unL = WL[1] * n[0] + WL[2] * n[1] + WL[3] * n[2];
   const real unR = WR[1] * n[0] + WR[2] * n[1] + WR[3] * n[2];
-  const real sL = dg_sqrt(WL[0]), sR = dg_sqrt(WR[0]);
+  // one reciprocal square root per side gives sqrt(rho), 1 / sqrt(rho) and 1 / rho; one more
+  // gives c and 1 / c^2 (FP64 divisions and square roots are long dependent sequences)
+  const real isL = dg_rsqrt(WL[0]), isR = dg_rsqrt(WR[0]);
+  const real sL = WL[0] * isL, sR = WR[0] * isR;
+  const real irL = isL * isL, irR = isR * isR;
   const real iws = real(1) / (sL + sR);
-  const real HL = (EL + WL[4]) / WL[0], HR = (ER + WR[4]) / WR[0];
+  const real HL = (EL + WL[4]) * irL, HR = (ER + WR[4]) * irR;
   real vel[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) vel[k] = (sL * WL[1 + k] + sR * WR[1 + k]) * iws;
   const real H = (sL * HL + sR * HR) * iws;
   const real q2 = vel[0] * vel[0] + vel[1] * vel[1] + vel[2] * vel[2];
   const real c2 = gm1 * (H - real(0.5) * q2);
-  const real c = dg_sqrt(c2);
-  const real ic2 = real(1) / c2;
+  const real ic = dg_rsqrt(c2);
+  const real c = c2 * ic;
+  const real ic2 = ic * ic;
   const real rho = sL * sR;
   const real un = vel[0] * n[0] + vel[1] * n[1] + vel[2] * n[2];
   const real dp = WR[4] - WL[4];
@@ -153,11 +158,11 @@ __device__ __forceinline__ void roe_vjp(const real WL[NV], const real WR[NV], co
   const real a1 = (dp - rho * c * dun) * real(0.5) * ic2;
   const real a5 = (dp + rho * c * dun) * real(0.5) * ic2;
   const real a2 = (WR[0] - WL[0]) - dp * ic2;
-  const real del = real(0.1) * c;
+  const real del = real(0.1) * c, idel = real(10) * ic;
   real l1, l2, l5, d1, d2, d5, e1, e2, e5;
-  absf_vjp(un - c, del, smooth, l1, d1, e1);
-  absf_vjp(un, del, smooth, l2, d2, e2);
-  absf_vjp(un + c, del, smooth, l5, d5, e5);
+  absf_vjp(un - c, del, idel, smooth, l1, d1, e1);
+  absf_vjp(un, del, idel, smooth, l2, d2, e2);
+  absf_vjp(un + c, del, idel, smooth, l5, d5, e5);
   const real w1 = l1 * a1, w5 = l5 * a5, w2 = l2 * a2, wt = l2 * rho;
   real dvt[3];
 #pragma unroll
@@ -216,7 +221,7 @@ __device__ __forceinline__ void roe_vjp(const real WL[NV], const real WR[NV], co
   // rho = sL sR
   real lsL = lrho * sR, lsR = lrho * sL;
   // ic2 = 1/c2, c = sqrt(c2)
-  real lc2 = -lic2 * ic2 * ic2 + lc * h / c;
+  real lc2 = -lic2 * ic2 * ic2 + lc * h * ic;
   // c2 = gm1 (H - q2/2)
   lH += gm1 * lc2;
   lq2 -= h * gm1 * lc2;
@@ -247,11 +252,12 @@ __device__ __forceinline__ void roe_vjp(const real WL[NV], const real WR[NV], co
   }
   lWR[0] += ldrho;
   lWL[0] -= ldrho;
-  // per side: HL = (EL + pL)/rhoL, sL = sqrt(rhoL), FL = euler_normal, EL, unL
-  auto side = [&](const real* W, real E, real unK, real HK, real sK, real lHK, real lsK, real* lW) {
-    real lE = lHK / W[0];
-    lW[4] += lHK / W[0];
-    lW[0] += -lHK * HK / W[0] + lsK * h / sK;
+  // per side: HL = (EL + pL)/rhoL, sL = sqrt(rhoL), FL = euler_normal, EL, unL; irK = 1/rho,
+  // isK = 1/sqrt(rho)
+  auto side = [&](const real* W, real E, real unK, real HK, real irK, real isK, real lHK, real lsK, real* lW) {
+    real lE = lHK * irK;
+    lW[4] += lHK * irK;
+    lW[0] += -lHK * HK * irK + lsK * h * isK;
     // F = (rho un, rho un u + p n, (E + p) un), weight 1/2
     const real lF0 = h * lf[0], lF4 = h * lf[4];
     real lunK = lF0 * W[0] + lF4 * (E + W[4]);
@@ -272,8 +278,8 @@ __device__ __forceinline__ void roe_vjp(const real WL[NV], const real WR[NV], co
     lW[4] += lE * ph.inv_gm1;
     lW[0] += lE * real(0.5) * (W[1] * W[1] + W[2] * W[2] + W[3] * W[3]);
   };
-  side(WL, EL, unL, HL, sL, lHL, lsL, lWL);
-  side(WR, ER, unR, HR, sR, lHR, lsR, lWR);
+  side(WL, EL, unL, HL, irL, isL, lHL, lsL, lWL);
+  side(WR, ER, unR, HR, irR, isR, lHR, lsR, lWR);
 }
 
 // ---------------------------------------------------------------------------
