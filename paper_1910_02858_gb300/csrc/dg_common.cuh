@@ -272,7 +272,7 @@ __device__ __forceinline__ void riemann_hllc(const real WL[NV], const real WR[NV
 // Roe flux (5-wave, frame-free); smooth != 0: Harten-type smoothing of |lambda| (below
 // delta = 0.1 c, (lambda^2 + delta^2) / (2 delta)).  Written as f = (S - D) / 2: the central
 // part S = F(W_L).n + F(W_R).n and the dissipation D = sum_k |lambda_k| alpha_k r_k with
-// Roe averages weighted by sqrt(rho); irL, irR = 1 / rho.  The two parts are independent, so
+// Roe averages weighted by sqrt(rho) (riemann_roe ignores irL, irR).  The two parts are independent, so
 // a kernel with few face nodes per SM computes them in separate warps.
 template <typename real>
 __device__ __forceinline__ void roe_central(const real WL[NV], const real WR[NV], const real n[3],
@@ -291,27 +291,28 @@ __device__ __forceinline__ void roe_central(const real WL[NV], const real WR[NV]
 }
 
 template <typename real>
-__device__ __forceinline__ void roe_dissipation(const real WL[NV], const real WR[NV], const real irL, const real irR,
-                                                const real n[3], const Phys<real>& ph, bool smooth, real D[NV]) {
+__device__ __forceinline__ void roe_dissipation(const real WL[NV], const real WR[NV], const real n[3],
+                                                const Phys<real>& ph, bool smooth, real D[NV]) {
   const real q2L = WL[1] * WL[1] + WL[2] * WL[2] + WL[3] * WL[3];
   const real q2R = WR[1] * WR[1] + WR[2] * WR[2] + WR[3] * WR[3];
   const real EL = WL[4] * ph.inv_gm1 + real(0.5) * WL[0] * q2L;
   const real ER = WR[4] * ph.inv_gm1 + real(0.5) * WR[0] * q2R;
-  // Roe averages (sqrt(rho_L) a_L + sqrt(rho_R) a_R) / (sqrt(rho_L) + sqrt(rho_R)) written
-  // with r = sqrt(rho_R / rho_L) as (a_L + r a_R) / (1 + r), and sqrt(rho_L rho_R) = rho_L r
-  const real r = dg_sqrt(WR[0] * irL);
-  const real iw = real(1) / (real(1) + r);
-  const real HL = (EL + WL[4]) * irL, HR = (ER + WR[4]) * irR;
+  // Roe averages (sqrt(rho_L) a_L + sqrt(rho_R) a_R) / (sqrt(rho_L) + sqrt(rho_R)); one
+  // reciprocal square root per side gives sqrt(rho) and, for the enthalpy,
+  // sqrt(rho) H = (E + p) / sqrt(rho)
+  const real isL = dg_rsqrt(WL[0]), isR = dg_rsqrt(WR[0]);
+  const real sL = WL[0] * isL, sR = WR[0] * isR;
+  const real iw = real(1) / (sL + sR);
   real vel[3];
 #pragma unroll
-  for (int c = 0; c < 3; ++c) vel[c] = dg_fma(r, WR[1 + c], WL[1 + c]) * iw;
-  const real H = dg_fma(r, HR, HL) * iw;
+  for (int c = 0; c < 3; ++c) vel[c] = dg_fma(sL, WL[1 + c], sR * WR[1 + c]) * iw;
+  const real H = dg_fma(EL + WL[4], isL, (ER + WR[4]) * isR) * iw;
   const real q2 = vel[0] * vel[0] + vel[1] * vel[1] + vel[2] * vel[2];
   const real c2 = ph.gm1 * (H - real(0.5) * q2);
   const real ic = dg_rsqrt(c2);  // c = c2 / sqrt(c2) and 1 / c2 from one reciprocal square root
   const real c = c2 * ic;
   const real ic2 = ic * ic;
-  const real rho = WL[0] * r;
+  const real rho = sL * sR;
   const real un = vel[0] * n[0] + vel[1] * n[1] + vel[2] * n[2];
   const real dp = WR[4] - WL[4];
   real dv[3];
@@ -346,7 +347,7 @@ __device__ __forceinline__ void riemann_roe(const real WL[NV], const real WR[NV]
                                             const real n[3], const Phys<real>& ph, bool smooth, real f[NV]) {
   real S[NV], D[NV];
   roe_central(WL, WR, n, ph, S);
-  roe_dissipation(WL, WR, irL, irR, n, ph, smooth, D);
+  roe_dissipation(WL, WR, n, ph, smooth, D);
 #pragma unroll
   for (int v = 0; v < NV; ++v) f[v] = real(0.5) * (S[v] - D[v]);
 }

@@ -1154,7 +1154,15 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(15 * n * n * n / 2) 
   const unsigned r = cluster_ctarank();
   const int kb = (int)(r ^ 1u) * hk;  // first k of the other half
   const int wp = tid >> 5, ln = tid & 31;
-  const int g = wp / NV, v = wp - g * NV;  // warp-uniform
+  // (g, v) of warp wp from a table that balances the FP64 warp instructions of the four SM
+  // sub-partitions (warp wp runs on sub-partition wp mod 4): one of the three energy-flux
+  // warps (v = 4, the longest) on each of sub-partitions 0-2, the primitive variables and
+  // no surface terms on sub-partition 3, which has three warps
+  //   wp: 0  1  2  3  4  5  6  7  8  9 10 11 12 13 14
+  //   g:  0  1  2  1  1  2  0  2  2  0  1  0  0  1  2
+  //   v:  4  4  4  1  0  0  0  2  1  1  2  3  2  3  3
+  const int g = (int)((0x24128964ull >> (2 * wp)) & 3ull);
+  const int v = (int)((0xda689400324ull >> (3 * wp)) & 7ull);  // warp-uniform
   const int e = blockIdx.x >> 1;           // grid = 2 K, clusters of two consecutive CTAs
   const int i = ln % n, j = (ln / n) % n, k = (int)r * hk + ln / n2;
   const int node = i + n * (j + n * k);
@@ -1175,15 +1183,18 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(15 * n * n * n / 2) 
     row[l] = Ja[((size_t)e * 9 + g * 3 + l) * n3 + node];
   }
   const real sj = sJ[(size_t)e * n3 + node];
-  if (g == 0) {  // W_v as cons_to_prim forms it
+  if ((wp & 3) == 3) {  // the primitive variables as cons_to_prim forms them: warps 3, 7, 11
     const real ir = real(1) / Uo[0];
     const real u = Uo[1] * ir, vv = Uo[2] * ir, w = Uo[3] * ir;
-    real Wv = Uo[0];
-    if (v == 1) Wv = u;
-    if (v == 2) Wv = vv;
-    if (v == 3) Wv = w;
-    if (v == 4) Wv = ph.gm1 * (Uo[4] - real(0.5) * (Uo[1] * u + Uo[2] * vv + Uo[3] * w));
-    sW[v * n3p + pn] = Wv;
+    if (wp == 3) {
+      sW[1 * n3p + pn] = u;
+      sW[2 * n3p + pn] = vv;
+    } else if (wp == 7) {
+      sW[0 * n3p + pn] = Uo[0];
+      sW[3 * n3p + pn] = w;
+    } else {
+      sW[4 * n3p + pn] = ph.gm1 * (Uo[4] - real(0.5) * (Uo[1] * u + Uo[2] * vv + Uo[3] * w));
+    }
   }
   __syncthreads();
   // BR1 surface terms of the face nodes that this half reads, one thread per (variable,
@@ -1191,7 +1202,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(15 * n * n * n / 2) 
   // [r n/2, (r + 1) n/2), then face 4 + r (Gauss-Lobatto: only the nodes on a face read it)
   // or both k faces (Gauss: every node reads both)
   constexpr int nIJq = 4 * (n2 / 2), nKf = LGL ? n2 : 2 * n2, nQ = nIJq + nKf;
-  for (int it = tid; it < NV * nQ; it += T) {
+  // on the twelve warps of sub-partitions 0-2 (dense index wq = wp - wp / 4)
+  const int wq = wp - (wp >> 2);
+  for (int it = (wp & 3) == 3 ? NV * nQ : wq * 32 + ln; it < NV * nQ; it += 12 * 32) {
     const int c = it / nQ, f = it - c * nQ;
     int s, pq;
     if (f < nIJq) {
@@ -1473,7 +1486,7 @@ __global__ void __launch_bounds__(128) k_face3(const real* __restrict__ Wf, cons
     }
     if constexpr (RS == 0) {
       if (role == 0)
-        roe_dissipation(WL, WR, real(1) / WL[0], real(1) / WR[0], nv, ph, ph.riemann == 2, out);
+        roe_dissipation(WL, WR, nv, ph, ph.riemann == 2, out);
       else
         roe_central(WL, WR, nv, ph, out);
     } else {
@@ -1704,7 +1717,7 @@ __global__ void __launch_bounds__(384) k_surf_face(
       }
       if constexpr (RS == 0) {
         if (role == 0)
-          roe_dissipation(WL, WR, real(1) / WL[0], real(1) / WR[0], nv, ph, ph.riemann == 2, out);
+          roe_dissipation(WL, WR, nv, ph, ph.riemann == 2, out);
         else
           roe_central(WL, WR, nv, ph, out);
       } else {
@@ -1783,12 +1796,13 @@ __global__ void __launch_bounds__(384) k_surf_face(
 // nodes that they lie on (faces 0-3 with q in that range, face 4 + r).  On Gauss-Lobatto
 // nodes a node receives the flux and gives the state of a face only where it lies on it,
 // so the two halves share nothing.  Warps are role-uniform, two per role over the half's
-// 48 face nodes, ordered so that each SM sub-partition gets the Riemann dissipation and the
-// central flux, or the two viscous fluxes (FP64 warp instructions, which hold a
-// sub-partition for 64 clocks whatever their active lanes, set the time here).  Fluxes,
-// update and face states use the expressions of k_surf_face.
+// 48 face nodes; FP64 warp instructions, which hold an SM sub-partition for 64 clocks
+// whatever their active lanes, set the time here, so the twelve warps are placed (warp w on
+// sub-partition w mod 4) to give each of the two longest chains, the Riemann dissipation
+// (or the whole Riemann flux), a sub-partition of its own, and the central and viscous
+// fluxes the other two.  Fluxes, update and face states use the expressions of k_surf_face.
 template <int RS>
-__global__ void __launch_bounds__(256) k_surf_face2(
+__global__ void __launch_bounds__(384) k_surf_face2(
     const double* __restrict__ WfIn, const double* __restrict__ Gf, const double* __restrict__ fgeo,
     const int* __restrict__ elemSide, const double* __restrict__ sJ, const double* __restrict__ Utv,
     double* __restrict__ U, double* __restrict__ dU, double* __restrict__ WfOut, const double* __restrict__ xsol,
@@ -1796,7 +1810,7 @@ __global__ void __launch_bounds__(256) k_surf_face2(
     unsigned* __restrict__ status) {
   using real = double;
   constexpr int n = 4, n2 = n * n, n3 = n2 * n, n3p = Cfg<n>::n3p, hk = n / 2, h3 = n3 / 2;
-  constexpr int R = RS == 0 ? 4 : 3, T = 2 * 32 * R;
+  constexpr int R = RS == 0 ? 4 : 3, T = 384;
   constexpr int FIJ = 4 * (n2 / 2), FH = FIJ + n2;  // face nodes of a half: faces 0-3, then face 4 + r
   static_assert(FH <= 64 && NV * h3 <= T, "two warps per role, one thread per (variable, node)");
   __shared__ real sf[R][NV][FH];
@@ -1834,11 +1848,16 @@ __global__ void __launch_bounds__(256) k_surf_face2(
   load_ops<real, n>(sOp, ops, tid, T);
   if (tid < 6) sES[tid] = elemSide[(size_t)e * 6 + tid];
   __syncthreads();
-  // a5: warp w takes role {0, 0, 1, 1, 3, 3, 2, 2}[w] (Roe) or {0, 0, 1, 1, 2, 2}[w]
+  // a5: roles of warps 0-11, -1 idle: Roe {0, 0, 3, 3, -, -, 1, 1, -, -, 2, 2} (dissipation on
+  // sub-partitions 0 and 1, central + viscous on 2 and 3), others {0, 0, 1, 1, -, -, 2, 2, -, ...}
   const int w = tid >> 5;
-  const int role = w < 2 ? 0 : (w < 4 ? 1 : (RS == 0 ? (w < 6 ? 3 : 2) : 2));
+  int role = -1;
+  if (w < 2) role = 0;
+  else if (w < 4) role = RS == 0 ? 3 : 1;
+  else if (w == 6 || w == 7) role = RS == 0 ? 1 : 2;
+  else if ((w == 10 || w == 11) && RS == 0) role = 2;
   const int fh = (w & 1) * 32 + ln;
-  if (fh < FH) {
+  if (role >= 0 && fh < FH) {
     int s, pq;
     face_node(fh, s, pq);
     const int es = sES[s];
@@ -1859,7 +1878,7 @@ __global__ void __launch_bounds__(256) k_surf_face2(
       }
       if constexpr (RS == 0) {
         if (role == 0)
-          roe_dissipation(WL, WR, real(1) / WL[0], real(1) / WR[0], nv, ph, ph.riemann == 2, out);
+          roe_dissipation(WL, WR, nv, ph, ph.riemann == 2, out);
         else
           roe_central(WL, WR, nv, ph, out);
       } else {

@@ -24,7 +24,7 @@ cudaError_t launch_surf_face(const DevMesh& m, const void* WfIn, void* WfOut, do
   if (m.n != 4) return cudaErrorInvalidValue;
   if (m.lgl && 2 * m.K <= m.nsm) {  // two CTAs per element
 #define FLEXI_SF2(RSV)                                                                                          \
-  k_surf_face2<RSV><<<2 * m.K, RSV == 0 ? 256 : 192, 0, st>>>(                                                 \
+  k_surf_face2<RSV><<<2 * m.K, 384, 0, st>>>(                                                 \
       (const double*)WfIn, (const double*)m.Gf, (const double*)m.fgeo, m.elemSide, (const double*)m.sJ,         \
       (const double*)m.Utv, U, dU, (double*)WfOut, m.xsol, rk, t, src, m.K, m.S, m.nBC, ops, ph, m.status)
     switch (ph.riemann) {
