@@ -868,7 +868,7 @@ def adjoint_fp32_error(dev, F, wl, Solver, SolverConfig, torch, final_state):
             UT = final_state(U0d, s, nsteps, dt, 0.0, 20)
             J = (wJ * 0.5 * (UT[:, 1] ** 2 + UT[:, 2] ** 2 + UT[:, 3] ** 2) / UT[:, 0]).sum()
             J.backward()
-            out[name] = (UT.detach().double(), U0d.grad.detach().double(), J.item())
+            out[name] = (UT.detach().double(), U0d.grad.detach().double(), J.detach().item())
         finally:
             s.close()
     (U64, g64, J64), (U32, g32, J32) = out["fp64"], out["fp32"]

@@ -107,7 +107,7 @@ def test_c5_gradient_fd_and_oracle(c5):
     # J = sum w J |m|^2 / (2 rho): its gradient with respect to U_T by the same reduction
     wJ = torch.tensor(_oracle(sk, mesh).quad_weights().numpy(), device=DEV).unsqueeze(1)
     J = (wJ[:, 0] * 0.5 * (UT[:, 1] ** 2 + UT[:, 2] ** 2 + UT[:, 3] ** 2) / UT[:, 0]).sum()
-    Jv = J.item()
+    Jv = J.detach().item()
     assert abs(Jv - _ke(s, UT.detach())) < 1e-12 * Jv
     J.backward()
     grad = U0d.grad.detach()
@@ -145,7 +145,7 @@ def test_c5_gradient_vs_oracle_adjoint(c5):
     J = (wJ * 0.5 * (UT[:, 1] ** 2 + UT[:, 2] ** 2 + UT[:, 3] ** 2) / UT[:, 0]).sum()
     J.backward()
     Jo, go = dg.gradient_ke(torch.tensor(U0), nsteps, dt)
-    assert abs(Jo - float(J)) < 1e-12 * abs(Jo)
+    assert abs(Jo - J.detach().item()) < 1e-12 * abs(Jo)
     assert float((U0d.grad.cpu() - go).norm() / go.norm()) < 1e-10
 
 
