@@ -157,7 +157,7 @@ def _c5_run(s, mesh, sk, U0, dtype):
     UT = final_state(U0d, s, 40, 1e-3, 0.0, 20)
     J = (wJ * 0.5 * (UT[:, 1] ** 2 + UT[:, 2] ** 2 + UT[:, 3] ** 2) / UT[:, 0]).sum()
     J.backward()
-    return UT.detach().double().cpu(), U0d.grad.detach().double().cpu(), float(J)
+    return UT.detach().double().cpu(), U0d.grad.detach().double().cpu(), J.detach().item()
 
 
 def test_c5_fp32_forward_and_adjoint_error(c5):
